@@ -1,0 +1,20 @@
+"""The oracle: a plain, slow, obviously correct CPU implementation of the
+FTKomega hot path (arXiv:1802.02854), in FP64.
+
+TEST INFRASTRUCTURE. Only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline / reference legs may import, call, link or execute anything
+under oracle/. The product package never does, and the oracle never imports
+the product package; the two share only the seeded input generators in
+ftk_inputs/.
+
+Parts:
+  dense.py    Kronecker-product H, canonical spectrum (Eq. chiAB), and the
+              same estimator the CUDA path computes, evaluated exactly in the
+              eigenbasis (N <= 12).
+  sparse.c    matrix-free H v, mTPQ, S^gamma_q, textbook shifted COCG
+              (projected and unprojected), canonical sum, Philox4x32-10.
+  reweight.py reading R1: mTPQ shells to temperatures via Eq. B1.
+
+Every function is pinned by -m "not gpu" tests (tests/test_oracle_*.py)
+against closed forms, brute force, invariants and published test vectors.
+"""
