@@ -189,7 +189,11 @@ NAMED = {
     4: (1, 2),
     6: (1, 3),
     8: (2, 2),
+    10: (1, 5),
     12: (2, 3),
+    14: (1, 7),
+    16: (2, 4),
+    20: (2, 5),
     18: (3, 3),
     24: (3, 4),
     26: [[3, 1], [-1, 4]],   # 13 cells: tilted, avoids the 1 x 13 double bonds

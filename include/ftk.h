@@ -1,0 +1,196 @@
+/*
+ * ftk.h -- C-ABI of the GB300 FTKomega hot path.
+ *
+ * Method: Yamaji, Suzuki, Kawamura, "Finite-temperature spectra of quantum
+ * lattice models by the shifted Krylov method and typical pure states"
+ * (arXiv:1802.02854). Every entry point cites the passage that defines the
+ * operation it performs.
+ *
+ * Conventions shared by all entry points
+ * -------------------------------------
+ * Basis (Sec. II.A): |x> = |sigma_0 ... sigma_{N-1}>, bit l of the index x is
+ *   site l, bit 1 = spin up. A state is 2^N complex amplitudes in index order.
+ * Precision: FTK_FP64 stores complex amplitudes as two doubles (16 B),
+ *   FTK_FP32 as two floats (8 B). All scalar inputs and outputs are double in
+ *   both modes; norms, inner products, TPQ statistics, Krylov scalars and
+ *   reweighting sums are always accumulated in double.
+ * Memory: device vectors live in ONE caller-allocated device workspace
+ *   (ftk_footprint gives its size, ftk_bind_workspace hands it over); the
+ *   library never allocates vector-sized memory itself. The context owns only
+ *   a few small device buffers (constants, scalars, reduction flags).
+ *   Host arrays are owned by the caller and only read/written during a call.
+ * Streams: all device work of a context is issued on opts.cuda_stream
+ *   (NULL = legacy default stream). Calls that return host results
+ *   synchronise that stream; the others are asynchronous.
+ * Threading: a context is used from one host thread at a time.
+ * Errors: every call returns an ftk_status; FTK_OK == 0. No exception or
+ *   longjmp crosses the ABI. ftk_last_error() returns a message for the last
+ *   failing call on that context. After FTK_ECUDA the context should be
+ *   destroyed.
+ */
+#ifndef FTK_H
+#define FTK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ftk_ctx ftk_ctx;
+
+typedef enum {
+    FTK_OK = 0,
+    FTK_EINVAL = 1,       /* invalid argument (message says which)              */
+    FTK_ENOMEM = 2,       /* workspace missing or too small                      */
+    FTK_ECUDA = 3,        /* a CUDA call failed                                  */
+    FTK_ENOCONV = 4,      /* Krylov solve hit max_iter; outputs still written    */
+    FTK_EBREAKDOWN = 5,   /* COCG breakdown (r^T r or p^T A p vanished)          */
+    FTK_ETIMEOUT = 6,     /* a bounded device wait gave up                       */
+    FTK_ETRUNC = 7,       /* reweighting series truncated for some temperature   */
+    FTK_EBUSY = 8         /* context busy / state missing for the request        */
+} ftk_status;
+
+enum { FTK_FP64 = 0, FTK_FP32 = 1 };
+enum { FTK_GAMMA_X = 0, FTK_GAMMA_Y = 1, FTK_GAMMA_Z = 2 };
+
+/* Cluster geometry: n_sites sites, pos[2*l], pos[2*l+1] = real-space (x, y)
+ * position R_l of site l (Sec. V: R_l is the site position, not the cell's). */
+typedef struct {
+    int32_t n_sites;
+    const double *pos;
+} ftk_lattice;
+
+/* One nearest-neighbour bond (i, j) of type gamma in {0=x, 1=y, 2=z}. */
+typedef struct {
+    int32_t i, j, gamma;
+} ftk_bond;
+
+typedef struct {
+    int32_t precision;    /* FTK_FP64 or FTK_FP32                                */
+    int32_t max_rhs;      /* right-hand sides per blocked solve (1..32)          */
+    int32_t n_saved;      /* shell states the workspace keeps (>= 1)             */
+    int32_t tile_bits;    /* amplitudes per CTA tile = 2^tile_bits; 0 = tuned    */
+    void *cuda_stream;    /* cudaStream_t, or NULL for the default stream        */
+} ftk_opts;
+
+/* Bytes of device workspace a context with these sizes needs (0 on bad
+ * arguments). Layout: 2 TPQ vectors + n_saved shells + max_rhs probe vectors
+ * + 3 * max_rhs Krylov vectors + reduction scratch. */
+size_t ftk_footprint(int32_t n_sites, int32_t n_saved, int32_t max_rhs, int32_t precision);
+
+/* Build a context for the Kitaev-Heisenberg Hamiltonian (Sec. V.A)
+ *   H = sum_<ij>_gamma J S_i.S_j + K S^gamma_i S^gamma_j
+ * on the given lattice/bond list. Requires 2 <= n_sites <= 30, bonds with
+ * 0 <= i, j < n_sites, i != j, gamma in {0, 1, 2}. Copies everything it needs
+ * (the caller may free lattice/bonds afterwards). Plans the tiled H.v passes
+ * (bonds whose two sites share a tile are applied in shared memory).
+ * On success *out receives the context. */
+ftk_status ftk_create(const ftk_lattice *lattice, const ftk_bond *bonds, int32_t n_bonds,
+                      double K, double J, const ftk_opts *opts, ftk_ctx **out);
+
+/* Hand the context a device workspace of at least ftk_footprint(...) bytes,
+ * 256-byte aligned. The caller keeps ownership and must keep it alive until
+ * ftk_destroy or the next bind. Rebinding discards TPQ and Krylov state. */
+ftk_status ftk_bind_workspace(ftk_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Seeded random initial state (Sec. II.A): c_x complex Gaussian, normalised
+ * (uniform on the unit sphere of R^{2 N_F}). Counter-based Philox4x32-10
+ * (Salmon et al. 2011): element x uses counter (x_lo, x_hi, sample, 0) and key
+ * (seed_lo, seed_hi); u1, u2 from the two 64-bit halves (>> 11, + 0.5, * 2^-53);
+ * Box-Muller c_x = sqrt(-2 ln u1) exp(2 pi i u2). Generated in double, stored
+ * in the context precision. ell is the mTPQ constant l of Eq. B1; it must be
+ * >= l_min = (1/N) sum_b lambda_max(h_b) so that l - H/N is positive
+ * semidefinite (else FTK_EINVAL). Resets the step counter to k = 0. */
+ftk_status ftk_tpq_init(ftk_ctx *ctx, uint64_t seed, uint32_t sample, double ell);
+
+/* Set the TPQ state to a caller vector (normalised by the call), e.g. for
+ * parity runs. v: 2^N complex amplitudes as interleaved (re, im) doubles,
+ * host (is_device = 0) or device (is_device = 1) memory. Same ell rules and
+ * reset as ftk_tpq_init. */
+ftk_status ftk_set_state(ftk_ctx *ctx, const double *v, int32_t is_device, double ell);
+
+/* n_steps mTPQ iterations (Appendix A, the (l - h)^k building block of
+ * Eq. B1): psi_{k+1} = (l - H/N) psi_k / q_k. For each input state k (from
+ * the current step on) the host arrays (length n_steps, may be NULL) receive
+ *   u_out[i]    = <psi_k|H|psi_k> / N
+ *   logQ_out[i] = log ||(l - H/N)^k psi_0||
+ *   h2_out[i]   = <psi_k|H^2|psi_k>
+ * and psi_k is kept as shell number k / save_every when k % save_every == 0
+ * (at most n_saved shells; FTK_ENOMEM if more are needed). Synchronises. */
+ftk_status ftk_tpq_step(ftk_ctx *ctx, int32_t n_steps, int32_t save_every,
+                        double *u_out, double *logQ_out, double *h2_out);
+
+/* Number of shells saved so far and, per shell, its step k and energy
+ * E_k = N u_k (host arrays of length >= n_saved, may be NULL). */
+ftk_status ftk_shells(const ftk_ctx *ctx, int32_t *n_out, int32_t *step_out, double *energy_out);
+
+/* Probe vector for the dynamical structure factor (Sec. V, S^alpha_{+Q}):
+ *   lambda = N^{-1/2} sum_l exp(+i q.R_l) S^gamma_l psi_shell
+ * written to probe slot rhs_slot (0 <= rhs_slot < max_rhs). q[2] is the
+ * momentum in the lattice's Cartesian frame. The slot remembers its shell
+ * (its energy sets the shift origin of ftk_shifted_cocg). Asynchronous. */
+ftk_status ftk_apply_op(ftk_ctx *ctx, int32_t shell, int32_t gamma, const double q[2],
+                        int32_t rhs_slot);
+
+/* Load probe slot rhs_slot with a caller vector lambda (host or device, same
+ * layout as ftk_set_state, not normalised) whose shift origin is energy. */
+ftk_status ftk_set_probe(ftk_ctx *ctx, int32_t rhs_slot, const double *v, int32_t is_device,
+                         double energy);
+
+/* Shifted COCG (Sec. II.B; BiCG with shadow conj(r) on the complex-symmetric
+ * z - H, Frommer 2003 for the shifts) for the probes in rhs_slots[0..n_rhs):
+ *   G_j(omega_s) = <lambda_j| (z_js - H)^{-1} |lambda_j>,  z_js = E_j + omega_s + i eta
+ * with E_j the slot's shift origin. The n_rhs solves run as one blocked
+ * iteration (one H.V over all of them per step) with per-RHS scalars; the
+ * seed shift of RHS j is z_j at omega[n_omega/2]. Solve j stops at the first
+ * iteration with max_s ||r_j|| / |pi_js| <= tol ||lambda_j||.
+ * G_out: host, [n_rhs][n_omega] complex as (re, im) doubles. iters_out: host
+ * [n_rhs] (may be NULL). Returns FTK_ENOCONV if some solve hit max_iter
+ * (G still written), FTK_EBREAKDOWN on breakdown. n_omega <= 4096. Synchronises. */
+ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *rhs_slots, int32_t n_rhs,
+                            const double *omega, int32_t n_omega, double eta,
+                            double tol, int32_t max_iter,
+                            double *G_out, int32_t *iters_out);
+
+/* Temperature sweep by reweighting the saved shells (reading R1 of the
+ * Taylor series Eq. B1; the shell-to-temperature map of Sec. III.D):
+ *   S(omega, T) = sum_s W_s(1/T) S_s(omega) / sum_s W_s(1/T),
+ *   S_s(omega) = -Im G_s(omega) / pi,
+ * with W_s the sum of the series weights w_n whose step floor(n/2) is nearest
+ * to shell s (ties to the later shell). G: host [n_shell][n_omega] complex
+ * (re, im) for shells 0..n_shell-1 of this context (their TPQ statistics are
+ * kept by the context). S_out: host [n_T][n_omega]. trunc_out: host [n_T]
+ * (may be NULL), 1 where the series tail exceeds 1e-14 of the total; then the
+ * call returns FTK_ETRUNC with S still written. Computed on the device in
+ * double. Synchronises. */
+ftk_status ftk_spectrum(ftk_ctx *ctx, const double *G, int32_t n_shell, int32_t n_omega,
+                        const double *T, int32_t n_T, double *S_out, int32_t *trunc_out);
+
+/* out = H v for n_rhs interleaved vectors (layout [2^N][n_rhs] complex in the
+ * context precision). v and out are device pointers, must not overlap, and
+ * need 16-byte alignment. The product of Sec. IV.A's cost unit ("a Lanczos
+ * step"); exposed for tests and the bandwidth metric. Asynchronous. */
+ftk_status ftk_hv(ftk_ctx *ctx, const void *v_dev, void *out_dev, int32_t n_rhs);
+
+/* Copy 2^N amplitudes of an internal vector to the host as (re, im) doubles:
+ * which = 0 current TPQ state (normalised), 1 + s shell s (normalised),
+ * -1 - j probe slot j. Synchronises. */
+ftk_status ftk_get_vector(ftk_ctx *ctx, int32_t which, double *host_out);
+
+/* Number of H.v passes the plan uses, and the tile bits. */
+ftk_status ftk_plan_info(const ftk_ctx *ctx, int32_t *n_passes, int32_t *tile_bits);
+
+/* Kernel launches issued by this context since creation (for accounting). */
+int64_t ftk_launch_count(const ftk_ctx *ctx);
+
+/* Message of the last failing call on ctx; with ctx == NULL, of the last
+ * failing ftk_create on this host thread. Valid until the next call. */
+const char *ftk_last_error(const ftk_ctx *ctx);
+void ftk_destroy(ftk_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTK_H */

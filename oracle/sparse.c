@@ -171,8 +171,12 @@ void orc_apply_op(int n_sites, const double *pos, int gamma, const double *q,
  * Projected (unprojected == 0): only lambda^dagger p^s and G are carried.
  * Unprojected (unprojected != 0): x^s and p^s vectors are carried explicitly
  * and G = lambda^dagger x^s at the end (independent check of the projection).
+ * A shift whose residual ||r_{k+1}|| / |pi^sigma_{k+1}| has dropped to
+ * tol ||lambda|| is frozen (no further updates of its pi, p, G): far from the
+ * seed |pi| grows geometrically and would overflow, while its remaining
+ * contributions are below the tolerance.
  * Stop after the first iteration k+1 with
- *   max_sigma ||r_{k+1}|| / |pi^sigma_{k+1}| <= tol ||lambda||.
+ *   max over unfrozen sigma of ||r_{k+1}|| / |pi^sigma_{k+1}| <= tol ||lambda||.
  * Returns 0 converged, 1 not converged, 2 breakdown.
  */
 int orc_cocg(int n_sites, int n_bonds, const int32_t *bonds, double K, double J,
@@ -186,6 +190,7 @@ int orc_cocg(int n_sites, int n_bonds, const int32_t *bonds, double K, double J,
     cplx *hp = malloc(d * sizeof(cplx)), *qv = malloc(d * sizeof(cplx));
     cplx *pi_prev = malloc(n_shift * sizeof(cplx)), *pi_cur = malloc(n_shift * sizeof(cplx));
     cplx *pt = calloc(n_shift, sizeof(cplx)), *beta_s = calloc(n_shift, sizeof(cplx));
+    char *frozen = calloc(n_shift, 1);
     cplx *xs = NULL, *ps = NULL;
     if (unprojected) {
         xs = calloc((size_t)n_shift * d, sizeof(cplx));
@@ -207,6 +212,7 @@ int orc_cocg(int n_sites, int n_bonds, const int32_t *bonds, double K, double J,
         cplx alpha = rho / pq;
         cplx g = dotc(d, lambda, r);                       /* lambda^dagger r_k */
         for (int s = 0; s < n_shift; ++s) {
+            if (frozen[s]) continue;
             cplx dz = z[s] - z_seed;
             cplx c = (k == 0) ? 0 : alpha * beta / alpha_prev;
             cplx pi_next = (1.0 + alpha * dz) * pi_cur[s] + c * (pi_cur[s] - pi_prev[s]);
@@ -234,7 +240,9 @@ int orc_cocg(int n_sites, int n_bonds, const int32_t *bonds, double K, double J,
         double rn = sqrt(creal(dotc(d, r, r)));
         worst = 0;
         for (int s = 0; s < n_shift; ++s) {
+            if (frozen[s]) continue;
             double rs = rn / cabs(pi_cur[s]);
+            if (rs <= tol * lnorm) frozen[s] = 1;
             if (rs > worst) worst = rs;
         }
         if (worst <= tol * lnorm) { status = 0; ++k; break; }
@@ -246,7 +254,7 @@ int orc_cocg(int n_sites, int n_bonds, const int32_t *bonds, double K, double J,
     *iters_out = k;
     *resid_out = worst / (lnorm > 0 ? lnorm : 1.0);
     free(r); free(p); free(hp); free(qv); free(pi_prev); free(pi_cur); free(pt);
-    free(beta_s); free(xs); free(ps);
+    free(beta_s); free(xs); free(ps); free(frozen);
     return status;
 }
 

@@ -1,0 +1,308 @@
+"""GB300 FTKomega hot path: Python binding of the C-ABI in include/ftk.h.
+
+The binding only marshals arguments: every step of the path runs in the
+CUDA kernels of libftk.so (paper_1802_02854_gb300/csrc). There is no CPU
+fallback: if the library is missing, importing works but every call raises
+FtkError telling how to build it. PyTorch provides device memory (the
+workspace tensor) and streams.
+
+Low-level functions carry the C names (ftk_create, ftk_tpq_step, ...);
+``Context`` bundles a context with its workspace tensor.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libftk.so")
+
+FTK_OK, FTK_EINVAL, FTK_ENOMEM, FTK_ECUDA, FTK_ENOCONV, FTK_EBREAKDOWN, FTK_ETIMEOUT, FTK_ETRUNC, FTK_EBUSY = range(9)
+FTK_FP64, FTK_FP32 = 0, 1
+STATUS_NAMES = ["FTK_OK", "FTK_EINVAL", "FTK_ENOMEM", "FTK_ECUDA", "FTK_ENOCONV", "FTK_EBREAKDOWN",
+                "FTK_ETIMEOUT", "FTK_ETRUNC", "FTK_EBUSY"]
+
+# Every symbol declared in include/ftk.h.
+EXPORTS = ["ftk_footprint", "ftk_create", "ftk_bind_workspace", "ftk_tpq_init", "ftk_set_state",
+           "ftk_tpq_step", "ftk_shells", "ftk_apply_op", "ftk_set_probe", "ftk_shifted_cocg",
+           "ftk_spectrum", "ftk_hv", "ftk_get_vector", "ftk_plan_info", "ftk_launch_count",
+           "ftk_last_error", "ftk_destroy"]
+
+
+class FtkError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class _Lattice(C.Structure):
+    _fields_ = [("n_sites", C.c_int32), ("pos", C.POINTER(C.c_double))]
+
+
+class _Bond(C.Structure):
+    _fields_ = [("i", C.c_int32), ("j", C.c_int32), ("gamma", C.c_int32)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_rhs", C.c_int32), ("n_saved", C.c_int32),
+                ("tile_bits", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libftk.so (built by paper_1802_02854_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FtkError(FTK_ECUDA, f"{LIB_PATH} not built; run paper_1802_02854_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    pd = C.POINTER(C.c_double)
+    pi = C.POINTER(C.c_int32)
+    L.ftk_footprint.argtypes = [i32, i32, i32, i32]
+    L.ftk_footprint.restype = C.c_size_t
+    L.ftk_create.argtypes = [C.POINTER(_Lattice), C.POINTER(_Bond), i32, dbl, dbl, C.POINTER(_Opts), C.POINTER(vp)]
+    L.ftk_bind_workspace.argtypes = [vp, vp, C.c_size_t]
+    L.ftk_tpq_init.argtypes = [vp, C.c_uint64, C.c_uint32, dbl]
+    L.ftk_set_state.argtypes = [vp, vp, i32, dbl]
+    L.ftk_tpq_step.argtypes = [vp, i32, i32, pd, pd, pd]
+    L.ftk_shells.argtypes = [vp, pi, pi, pd]
+    L.ftk_apply_op.argtypes = [vp, i32, i32, pd, i32]
+    L.ftk_set_probe.argtypes = [vp, i32, vp, i32, dbl]
+    L.ftk_shifted_cocg.argtypes = [vp, pi, i32, pd, i32, dbl, dbl, i32, pd, pi]
+    L.ftk_spectrum.argtypes = [vp, pd, i32, i32, pd, i32, pd, pi]
+    L.ftk_hv.argtypes = [vp, vp, vp, i32]
+    L.ftk_get_vector.argtypes = [vp, i32, pd]
+    L.ftk_plan_info.argtypes = [vp, pi, pi]
+    L.ftk_launch_count.argtypes = [vp]
+    L.ftk_launch_count.restype = i64
+    L.ftk_last_error.argtypes = [vp]
+    L.ftk_last_error.restype = C.c_char_p
+    L.ftk_destroy.argtypes = [vp]
+    L.ftk_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("ftk_footprint", "ftk_launch_count", "ftk_last_error", "ftk_destroy"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32)) if a is not None else None
+
+
+def _check(ctx, st, ok=(FTK_OK,)):
+    if st not in ok:
+        msg = lib().ftk_last_error(ctx).decode()
+        raise FtkError(st, msg)
+    return st
+
+
+# ----------------------------------------------------------- C-named wrappers
+def ftk_footprint(n_sites, n_saved, max_rhs, precision):
+    return int(lib().ftk_footprint(n_sites, n_saved, max_rhs, precision))
+
+
+def ftk_create(n_sites, pos, bonds, K, J, precision=FTK_FP64, max_rhs=1, n_saved=1, tile_bits=0,
+               stream=None):
+    """pos: float64 [N, 2]; bonds: int [n_bonds, 3] rows (i, j, gamma). Returns the context handle."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1)
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 3)
+    lat = _Lattice(int(n_sites), pos.ctypes.data_as(C.POINTER(C.c_double)))
+    barr = (_Bond * len(bonds))(*[_Bond(int(i), int(j), int(g)) for i, j, g in bonds])
+    opts = _Opts(int(precision), int(max_rhs), int(n_saved), int(tile_bits),
+                 C.c_void_p(int(stream) if stream else 0))
+    out = C.c_void_p()
+    st = lib().ftk_create(C.byref(lat), barr, len(bonds), float(K), float(J), C.byref(opts), C.byref(out))
+    _check(None, st)
+    return out.value
+
+
+def ftk_bind_workspace(ctx, dev_ptr, nbytes):
+    _check(ctx, lib().ftk_bind_workspace(ctx, C.c_void_p(dev_ptr), nbytes))
+
+
+def ftk_tpq_init(ctx, seed, sample, ell):
+    _check(ctx, lib().ftk_tpq_init(ctx, seed, sample, ell))
+
+
+def ftk_set_state(ctx, v, ell):
+    """v: complex128 host array (numpy) or a device pointer (int)."""
+    if isinstance(v, int):
+        _check(ctx, lib().ftk_set_state(ctx, C.c_void_p(v), 1, ell))
+    else:
+        a = np.ascontiguousarray(v, dtype=np.complex128)
+        _check(ctx, lib().ftk_set_state(ctx, a.ctypes.data_as(C.c_void_p), 0, ell))
+
+
+def ftk_tpq_step(ctx, n_steps, save_every):
+    u = np.zeros(n_steps)
+    lq = np.zeros(n_steps)
+    h2 = np.zeros(n_steps)
+    _check(ctx, lib().ftk_tpq_step(ctx, n_steps, save_every, _dp(u), _dp(lq), _dp(h2)))
+    return u, lq, h2
+
+
+def ftk_shells(ctx, cap=4096):
+    n = C.c_int32()
+    steps = np.zeros(cap, dtype=np.int32)
+    en = np.zeros(cap)
+    _check(ctx, lib().ftk_shells(ctx, C.byref(n), _ip(steps), _dp(en)))
+    return steps[: n.value].copy(), en[: n.value].copy()
+
+
+def ftk_apply_op(ctx, shell, gamma, q, slot):
+    qq = np.ascontiguousarray(q, dtype=np.float64)
+    _check(ctx, lib().ftk_apply_op(ctx, shell, gamma, _dp(qq), slot))
+
+
+def ftk_set_probe(ctx, slot, v, energy):
+    if isinstance(v, int):
+        _check(ctx, lib().ftk_set_probe(ctx, slot, C.c_void_p(v), 1, energy))
+    else:
+        a = np.ascontiguousarray(v, dtype=np.complex128)
+        _check(ctx, lib().ftk_set_probe(ctx, slot, a.ctypes.data_as(C.c_void_p), 0, energy))
+
+
+def ftk_shifted_cocg(ctx, slots, omega, eta, tol, max_iter, allow_noconv=False):
+    """Returns (G complex128 [n_rhs, n_omega], iters int32 [n_rhs], status)."""
+    sl = np.ascontiguousarray(slots, dtype=np.int32)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    G = np.zeros((len(sl), len(om)), dtype=np.complex128)
+    it = np.zeros(len(sl), dtype=np.int32)
+    ok = (FTK_OK, FTK_ENOCONV) if allow_noconv else (FTK_OK,)
+    st = _check(ctx, lib().ftk_shifted_cocg(ctx, _ip(sl), len(sl), _dp(om), len(om), eta, tol, max_iter,
+                                            G.ctypes.data_as(C.POINTER(C.c_double)), _ip(it)), ok)
+    return G, it, st
+
+
+def ftk_spectrum(ctx, G, T):
+    """G: complex128 [n_shell, n_omega]; returns (S [n_T, n_omega], trunc [n_T])."""
+    G = np.ascontiguousarray(G, dtype=np.complex128)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    S = np.zeros((len(T), G.shape[1]))
+    tr = np.zeros(len(T), dtype=np.int32)
+    _check(ctx, lib().ftk_spectrum(ctx, G.ctypes.data_as(C.POINTER(C.c_double)), G.shape[0], G.shape[1],
+                                   _dp(T), len(T), _dp(S), _ip(tr)), (FTK_OK, FTK_ETRUNC))
+    return S, tr
+
+
+def ftk_hv(ctx, v_ptr, out_ptr, n_rhs):
+    _check(ctx, lib().ftk_hv(ctx, C.c_void_p(v_ptr), C.c_void_p(out_ptr), n_rhs))
+
+
+def ftk_get_vector(ctx, which, dim):
+    out = np.zeros(dim, dtype=np.complex128)
+    _check(ctx, lib().ftk_get_vector(ctx, which, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def ftk_plan_info(ctx):
+    n = C.c_int32()
+    b = C.c_int32()
+    _check(ctx, lib().ftk_plan_info(ctx, C.byref(n), C.byref(b)))
+    return n.value, b.value
+
+
+def ftk_launch_count(ctx):
+    return int(lib().ftk_launch_count(ctx))
+
+
+def ftk_destroy(ctx):
+    if ctx:
+        lib().ftk_destroy(ctx)
+
+
+# ----------------------------------------------------------------- wrapper
+class Context:
+    """A context plus the torch device workspace it runs in.
+
+    cluster: object with n_sites, pos [N, 2], bonds [n_bonds, 3].
+    precision: "fp64" or "fp32". stream: torch.cuda.Stream (default: a new one).
+    """
+
+    def __init__(self, cluster, K, J, precision="fp64", max_rhs=1, n_saved=1, tile_bits=0, stream=None,
+                 workspace=None):
+        import torch
+
+        self.torch = torch
+        self.n = int(cluster.n_sites)
+        self.dim = 1 << self.n
+        self.prec = FTK_FP64 if precision in ("fp64", FTK_FP64) else FTK_FP32
+        self.max_rhs = max_rhs
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.handle = ftk_create(self.n, cluster.pos, cluster.bonds, K, J, self.prec, max_rhs, n_saved,
+                                 tile_bits, self.stream.cuda_stream)
+        self.bytes = ftk_footprint(self.n, n_saved, max_rhs, self.prec)
+        if workspace is None:
+            workspace = torch.empty(self.bytes, dtype=torch.uint8, device="cuda")
+        self.workspace = workspace
+        torch.cuda.synchronize()
+        ftk_bind_workspace(self.handle, workspace.data_ptr(), workspace.numel())
+
+    # thin method forms of the C calls
+    def tpq_init(self, seed, sample=0, ell=0.5):
+        ftk_tpq_init(self.handle, seed, sample, ell)
+
+    def set_state(self, v, ell=0.5):
+        ftk_set_state(self.handle, v, ell)
+
+    def tpq_step(self, n_steps, save_every):
+        return ftk_tpq_step(self.handle, n_steps, save_every)
+
+    def shells(self):
+        return ftk_shells(self.handle)
+
+    def apply_op(self, shell, gamma, q, slot):
+        ftk_apply_op(self.handle, shell, gamma, q, slot)
+
+    def set_probe(self, slot, v, energy):
+        ftk_set_probe(self.handle, slot, v, energy)
+
+    def shifted_cocg(self, slots, omega, eta, tol=1e-4, max_iter=10000, allow_noconv=False):
+        return ftk_shifted_cocg(self.handle, slots, omega, eta, tol, max_iter, allow_noconv)
+
+    def spectrum(self, G, T):
+        return ftk_spectrum(self.handle, G, T)
+
+    def hv(self, v, out=None):
+        """v: torch tensor [dim] or [dim, B] of complex128/complex64 on cuda."""
+        torch = self.torch
+        n_rhs = 1 if v.dim() == 1 else v.shape[1]
+        if out is None:
+            out = torch.empty_like(v)
+        cur = torch.cuda.current_stream()
+        self.stream.wait_stream(cur)
+        ftk_hv(self.handle, v.data_ptr(), out.data_ptr(), n_rhs)
+        cur.wait_stream(self.stream)
+        return out
+
+    def get_vector(self, which):
+        return ftk_get_vector(self.handle, which, self.dim)
+
+    def plan_info(self):
+        return ftk_plan_info(self.handle)
+
+    def launch_count(self):
+        return ftk_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            ftk_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

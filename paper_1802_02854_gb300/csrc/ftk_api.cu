@@ -1,0 +1,875 @@
+// Host runtime and C-ABI of the FTKomega hot path: context, H.v pass planner,
+// workspace carving, CUDA-graph captured Krylov chunks, autotuned tiles.
+#include "../../include/ftk.h"
+#include "ftk_common.cuh"
+#include "ftk_kernels.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace ftk;
+
+namespace {
+
+const size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Bond { int i, j, g; double par, anti, dg; };
+
+// Workspace regions (bytes from the workspace base).
+struct Layout {
+    size_t psi[2], shells, probes, kry[3], partials, shift, omega, gbuf, tbuf, total;
+    size_t vec_bytes;
+};
+
+const size_t kPartialsBytes = size_t(4) << 20;
+const int kShiftArrays = 5;
+
+Layout make_layout(int n, int n_saved, int max_rhs, int prec) {
+    Layout L{};
+    const size_t es = prec == FTK_FP64 ? 16 : 8;
+    const size_t vb = (size_t(1) << n) * es;
+    size_t off = 0;
+    L.vec_bytes = vb;
+    // the mTPQ state is always FP64 (16 B / amplitude); shells, probes and
+    // Krylov vectors use the context precision
+    const size_t vb64 = (size_t(1) << n) * 16;
+    for (int i = 0; i < 2; ++i) { L.psi[i] = off; off = align_up(off + vb64); }
+    L.shells = off; off = align_up(off + vb * n_saved);
+    L.probes = off; off = align_up(off + vb * max_rhs);
+    for (int i = 0; i < 3; ++i) { L.kry[i] = off; off = align_up(off + vb * max_rhs); }
+    L.partials = off; off = align_up(off + kPartialsBytes);
+    L.shift = off; off = align_up(off + size_t(kShiftArrays) * max_rhs * FTK_MAX_OMEGA * 16);
+    L.omega = off; off = align_up(off + FTK_MAX_OMEGA * 8);
+    L.gbuf = off; off = align_up(off + size_t(1024) * FTK_MAX_OMEGA * 16);   // spectrum input G
+    L.tbuf = off; off = align_up(off + 1024 * 8);
+    L.total = off;
+    return L;
+}
+
+// Small device buffers owned by the context.
+struct Small {
+    TpqState tpq;
+    unsigned int counters[8];
+    double hv_dots[FTK_MAX_RHS * FTK_HV_DOTS];
+    double upd_dots[FTK_MAX_RHS * FTK_UPD_DOTS];
+    double op_dots[4];
+    double inv_pi_max[2 * FTK_MAX_RHS];
+    int all_done;
+    int pad;
+    CocgSeed seed[FTK_MAX_RHS];
+};
+
+struct Plan {
+    int tile_bits = 0, chunk_bits = 0, threads = 512, grid = 0;
+    size_t smem = 0;
+    std::vector<PassDesc> passes;
+};
+
+}  // namespace
+
+struct ftk_ctx {
+    int n = 0, nb = 0, prec = 0, max_rhs = 1, n_saved_cap = 1, tile_bits_req = 0;
+    uint64_t dim = 0;
+    double K = 0, J = 0, ell_min = 0;
+    std::vector<Bond> bonds;
+    std::vector<double> pos;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int n_sm = 0, device = 0;
+    Small *dsmall = nullptr;         // device
+    double *stats = nullptr;         // device [3][cap]: u, logq, h2
+    int stats_cap = 0;
+    double *shell_scale = nullptr;   // device [n_saved_cap]
+    double *slot_energy = nullptr;   // device [max_rhs]
+    double *slot_norm2 = nullptr;    // device [max_rhs]
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    Layout L{};
+    // host mirrors
+    int k = 0, n_saved = 0, save_every = 1, have_state = 0;
+    double ell = 0.5;
+    std::vector<int> shell_step;
+    std::vector<int> slot_valid;
+    std::map<int, Plan> plans;       // by (precision, block width B): key prec * 64 + B
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;   // message of the last failed ftk_create
+
+ftk_status fail(ftk_ctx *c, ftk_status s, const std::string &m) {
+    if (c) c->err = m;
+    else g_create_err = m;
+    return s;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, FTK_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define LAUNCH(call)        \
+    do {                    \
+        CK(call);           \
+        ++ctx->launches;    \
+    } while (0)
+
+int elem_bytes(int prec) { return prec == FTK_FP64 ? 16 : 8; }
+
+// Greedy cover of the bonds by tile bit sets. The first pass takes the low
+// tile_bits sites (good when sites are labelled so that neighbours have close
+// numbers); each later pass keeps the chunk_bits lowest sites (coalescing)
+// and adds, one at a time, the site that completes most remaining bonds.
+bool plan_passes(ftk_ctx *ctx, int prec, int B, int tile_bits, Plan &pl) {
+    const int n = ctx->n;
+    const int es = elem_bytes(prec);
+    int c = 0;
+    while (c < n && (size_t(1) << c) * B * es < 256) ++c;   // >= 256 B contiguous runs
+    int b = std::min(tile_bits, n);
+    if (b < n && c > b - 2) c = std::max(0, b - 2);   // later passes need >= 2 free tile bits
+    if (c > b) c = b;
+    pl.tile_bits = b;
+    pl.chunk_bits = c;
+    pl.passes.clear();
+    std::vector<int> remaining(ctx->nb);
+    for (int q = 0; q < ctx->nb; ++q) remaining[q] = q;
+    std::vector<int> T;
+    for (int s = 0; s < b; ++s) T.push_back(s);
+    for (int guard = 0; guard < 64; ++guard) {
+        std::vector<char> in_t(n, 0);
+        for (int s : T) in_t[s] = 1;
+        std::vector<int> take, rest;
+        for (int q : remaining) {
+            const Bond &bd = ctx->bonds[q];
+            if (in_t[bd.i] && in_t[bd.j] && (int)take.size() < FTK_MAX_PASS_BONDS) take.push_back(q);
+            else rest.push_back(q);
+        }
+        if (take.empty() && !remaining.empty()) return false;
+        std::sort(T.begin(), T.end());
+        PassDesc pd;
+        memset(&pd, 0, sizeof pd);
+        pd.n_sites = n;
+        pd.tile_bits = b;
+        pd.chunk_bits = c;
+        pd.n_free = n - b;
+        int tpos[FTK_MAX_SITES];
+        for (int s = 0; s < n; ++s) tpos[s] = -1;
+        for (int k = 0; k < b; ++k) { pd.tile_pos[k] = T[k]; tpos[T[k]] = k; }
+        int f = 0;
+        for (int s = 0; s < n; ++s) if (!in_t[s]) pd.free_pos[f++] = s;
+        pd.n_bonds = (int)take.size();
+        for (int l = 0; l < pd.n_bonds; ++l) {
+            const Bond &bd = ctx->bonds[take[l]];
+            pd.bi[l] = tpos[bd.i];
+            pd.bj[l] = tpos[bd.j];
+            pd.par[l] = bd.par;
+            pd.anti[l] = bd.anti;
+            pd.par_f[l] = (float)bd.par;
+            pd.anti_f[l] = (float)bd.anti;
+            pd.dgc[l] = bd.g == 2 ? 1 : 0;
+        }
+        pd.dgv[0] = ctx->J / 4;
+        pd.dgv[1] = (ctx->J + ctx->K) / 4;
+        pd.dgv_f[0] = (float)pd.dgv[0];
+        pd.dgv_f[1] = (float)pd.dgv[1];
+        pl.passes.push_back(pd);
+        remaining = rest;
+        if (remaining.empty()) break;
+        // next tile set
+        T.clear();
+        std::vector<char> in2(n, 0);
+        for (int s = 0; s < c; ++s) { T.push_back(s); in2[s] = 1; }
+        while ((int)T.size() < b) {
+            int best = -1;
+            long best_score = -1;
+            for (int s = 0; s < n; ++s) {
+                if (in2[s]) continue;
+                long done = 0, touch = 0;
+                for (int q : remaining) {
+                    const Bond &bd = ctx->bonds[q];
+                    const bool hi = bd.i == s || bd.j == s;
+                    if (!hi) continue;
+                    ++touch;
+                    const int other = bd.i == s ? bd.j : bd.i;
+                    if (in2[other]) ++done;
+                }
+                const long score = done * 1000 + touch;
+                if (score > best_score) { best_score = score; best = s; }
+            }
+            T.push_back(best);
+            in2[best] = 1;
+        }
+    }
+    if (!remaining.empty()) return false;
+    const int np = (int)pl.passes.size();
+    for (int p = 0; p < np; ++p) {
+        pl.passes[p].first = p == 0;
+        pl.passes[p].last = p == np - 1;
+    }
+    return true;
+}
+
+ftk_status get_plan(ftk_ctx *ctx, int prec, int B, Plan **out) {
+    auto it = ctx->plans.find(prec * 64 + B);
+    if (it != ctx->plans.end()) { *out = &it->second; return FTK_OK; }
+    const int es = elem_bytes(prec);
+    int tb = ctx->tile_bits_req;
+    if (tb <= 0) {
+        // default: ~96 KB of tile per CTA (two CTAs per SM), at most 14 bits
+        tb = 0;
+        while ((size_t(2) << tb) * B * es <= size_t(96) << 10 && tb < 14) ++tb;
+    }
+    tb = std::max(2, std::min(tb, ctx->n));
+    while (tb > 2 && (size_t(1) << tb) * B * es > (size_t(200) << 10)) --tb;   // shared-memory cap
+    Plan pl;
+    if (!plan_passes(ctx, prec, B, tb, pl))
+        return fail(ctx, FTK_EINVAL, "H.v pass planning failed (tile too small for the bond list)");
+    pl.threads = std::min(B >= 8 ? 256 : 512, std::max(32, (1 << pl.tile_bits)));
+    pl.smem = hv_smem_bytes(prec, B, pl.tile_bits, pl.chunk_bits, pl.threads);
+    if (pl.smem > (size_t(227) << 10))
+        return fail(ctx, FTK_EINVAL, "tile does not fit in shared memory");
+    int per_sm = 1;
+    // occupancy: shared memory bound (228 KB per SM incl. 1 KB per CTA reserve)
+    per_sm = std::max(1, (int)((size_t(228) << 10) / (pl.smem + 1024)));
+    per_sm = std::min(per_sm, 2048 / pl.threads);
+    const long n_tiles = 1L << (ctx->n - pl.tile_bits);
+    pl.grid = (int)std::min<long>(n_tiles, (long)per_sm * ctx->n_sm);
+    if (pl.grid < 1) pl.grid = 1;
+    auto res = ctx->plans.emplace(prec * 64 + B, pl);
+    *out = &res.first->second;
+    return FTK_OK;
+}
+
+char *wsp(ftk_ctx *ctx, size_t off) { return ctx->ws + off; }
+
+int vec_grid(ftk_ctx *ctx, uint64_t n_items) {
+    const uint64_t want = (n_items + 255) / 256;
+    const uint64_t cap = uint64_t(4) * ctx->n_sm;
+    return (int)std::max<uint64_t>(1, std::min(want, cap));
+}
+
+// H.V over all passes. The last pass uses epilogue epi, earlier ones write
+// or accumulate the partial product into out.
+ftk_status run_hv(ftk_ctx *ctx, int prec, int B, int epi, const void *in, void *out, EpiArgs ea) {
+    Plan *pl = nullptr;
+    ftk_status s = get_plan(ctx, prec, B, &pl);
+    if (s != FTK_OK) return s;
+    const int np = (int)pl->passes.size();
+    for (int p = 0; p < np; ++p) {
+        const int e = (p == np - 1) ? epi : EPI_PLAIN;
+        LAUNCH(launch_hv_pass(prec, B, e, in, out, pl->passes[p], ea, pl->grid, pl->threads,
+                              pl->smem, ctx->stream));
+    }
+    return FTK_OK;
+}
+
+ftk_status ensure_stats(ftk_ctx *ctx, int need) {
+    if (need <= ctx->stats_cap) return FTK_OK;
+    int cap = std::max(need, std::max(1024, ctx->stats_cap * 2));
+    double *nb = nullptr;
+    CK(cudaMalloc(&nb, size_t(3) * cap * sizeof(double)));
+    CK(cudaMemsetAsync(nb, 0, size_t(3) * cap * sizeof(double), ctx->stream));
+    if (ctx->stats) {
+        for (int a = 0; a < 3; ++a)
+            CK(cudaMemcpyAsync(nb + size_t(a) * cap, ctx->stats + size_t(a) * ctx->stats_cap,
+                               ctx->stats_cap * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->stats);
+    }
+    ctx->stats = nb;
+    ctx->stats_cap = cap;
+    return FTK_OK;
+}
+
+double *stat_u(ftk_ctx *c) { return c->stats; }
+double *stat_lq(ftk_ctx *c) { return c->stats + c->stats_cap; }
+double *stat_h2(ftk_ctx *c) { return c->stats + 2 * size_t(c->stats_cap); }
+
+ftk_status check_ready(ftk_ctx *ctx) {
+    if (!ctx) return FTK_EINVAL;
+    if (!ctx->ws) return fail(ctx, FTK_ENOMEM, "no workspace bound");
+    return FTK_OK;
+}
+
+ftk_status check_ell(ftk_ctx *ctx, double ell) {
+    if (!(ell >= ctx->ell_min - 1e-12))
+        return fail(ctx, FTK_EINVAL, "ell below l_min = (1/N) sum_b lambda_max(h_b) = " +
+                                         std::to_string(ctx->ell_min));
+    return FTK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ftk_footprint(int32_t n_sites, int32_t n_saved, int32_t max_rhs, int32_t precision) {
+    if (n_sites < 2 || n_sites > FTK_MAX_SITES || n_saved < 1 || max_rhs < 1 ||
+        max_rhs > FTK_MAX_RHS || (precision != FTK_FP64 && precision != FTK_FP32))
+        return 0;
+    return make_layout(n_sites, n_saved, max_rhs, precision).total;
+}
+
+ftk_status ftk_create(const ftk_lattice *lat, const ftk_bond *bonds, int32_t n_bonds, double K,
+                      double J, const ftk_opts *opts, ftk_ctx **out) {
+    if (!out) return fail(nullptr, FTK_EINVAL, "null output handle");
+    *out = nullptr;
+    if (!lat || !bonds || !opts || !lat->pos) return fail(nullptr, FTK_EINVAL, "null argument");
+    const int n = lat->n_sites;
+    if (n < 2 || n > FTK_MAX_SITES) return fail(nullptr, FTK_EINVAL, "n_sites must be in [2, 30]");
+    if (n_bonds < 1 || n_bonds > 2 * FTK_MAX_PASS_BONDS) return fail(nullptr, FTK_EINVAL, "bad n_bonds");
+    if (opts->precision != FTK_FP64 && opts->precision != FTK_FP32)
+        return fail(nullptr, FTK_EINVAL, "precision must be FTK_FP64 or FTK_FP32");
+    if (opts->max_rhs < 1 || opts->max_rhs > FTK_MAX_RHS || opts->n_saved < 1)
+        return fail(nullptr, FTK_EINVAL, "max_rhs must be in [1, 32] and n_saved >= 1");
+    if (!std::isfinite(K) || !std::isfinite(J)) return fail(nullptr, FTK_EINVAL, "K, J must be finite");
+    for (int q = 0; q < n_bonds; ++q) {
+        const ftk_bond &b = bonds[q];
+        if (b.i < 0 || b.j < 0 || b.i >= n || b.j >= n || b.i == b.j || b.gamma < 0 || b.gamma > 2)
+            return fail(nullptr, FTK_EINVAL, "bond " + std::to_string(q) + " out of range");
+    }
+    ftk_ctx *ctx = new (std::nothrow) ftk_ctx();
+    if (!ctx) return FTK_ENOMEM;
+    ctx->n = n;
+    ctx->nb = n_bonds;
+    ctx->dim = uint64_t(1) << n;
+    ctx->K = K;
+    ctx->J = J;
+    ctx->prec = opts->precision;
+    ctx->max_rhs = opts->max_rhs;
+    ctx->n_saved_cap = opts->n_saved;
+    ctx->tile_bits_req = opts->tile_bits;
+    ctx->pos.assign(lat->pos, lat->pos + 2 * n);
+    // Matrix elements of h_b = J S_i.S_j + K S^g_i S^g_j on the S^z basis:
+    //   S^x S^x |x> = 1/4 |x'>, S^y S^y |x> = -s_i s_j / 4 |x'>, S^z S^z = s_i s_j / 4
+    // with x' = x ^ 2^i ^ 2^j, so for parallel (p) / antiparallel (a) spins
+    //   x-bond: p K/4,  a K/4 + J/2;  y-bond: p -K/4, a K/4 + J/2;  z-bond: p 0, a J/2
+    // and the diagonal is +dg (p) / -dg (a) with dg = J/4 (x, y), (J + K)/4 (z).
+    for (int q = 0; q < n_bonds; ++q) {
+        Bond bd;
+        bd.i = bonds[q].i;
+        bd.j = bonds[q].j;
+        bd.g = bonds[q].gamma;
+        if (bd.g == 0) { bd.par = K / 4; bd.anti = K / 4 + J / 2; bd.dg = J / 4; }
+        else if (bd.g == 1) { bd.par = -K / 4; bd.anti = K / 4 + J / 2; bd.dg = J / 4; }
+        else { bd.par = 0; bd.anti = J / 2; bd.dg = (J + K) / 4; }
+        ctx->bonds.push_back(bd);
+    }
+    // l_min: the bond block has eigenvalues (J+K)/4 (x2), (J-K)/4, -(3J+K)/4
+    const double lmax = std::max({(J + K) / 4, (J - K) / 4, -(3 * J + K) / 4});
+    ctx->ell_min = n_bonds * lmax / n;
+    ctx->slot_valid.assign(ctx->max_rhs, 0);
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) { delete ctx; return fail(nullptr, FTK_ECUDA, cudaGetErrorString(e)); }
+    if (opts->cuda_stream) {
+        ctx->stream = (cudaStream_t)opts->cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete ctx; return fail(nullptr, FTK_ECUDA, cudaGetErrorString(e)); }
+        ctx->own_stream = true;
+    }
+    e = cudaMalloc(&ctx->dsmall, sizeof(Small));
+    if (e == cudaSuccess) e = cudaMemset(ctx->dsmall, 0, sizeof(Small));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->shell_scale, sizeof(double) * ctx->n_saved_cap);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->slot_energy, sizeof(double) * ctx->max_rhs);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->slot_norm2, sizeof(double) * ctx->max_rhs);
+    if (e != cudaSuccess) { ftk_destroy(ctx); return fail(nullptr, FTK_ECUDA, cudaGetErrorString(e)); }
+    e = init_kernel_attributes();
+    if (e != cudaSuccess) {
+        ftk_destroy(ctx);
+        return fail(nullptr, FTK_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+    }
+    Plan *pl = nullptr;
+    if (get_plan(ctx, ctx->prec, 1, &pl) != FTK_OK) {
+        std::string m = ctx->err;
+        ftk_destroy(ctx);
+        return fail(nullptr, FTK_EINVAL, m);
+    }
+    *out = ctx;
+    return FTK_OK;
+}
+
+ftk_status ftk_bind_workspace(ftk_ctx *ctx, void *dev_ptr, size_t bytes) {
+    if (!ctx) return FTK_EINVAL;
+    if (!dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) % kAlign) != 0)
+        return fail(ctx, FTK_EINVAL, "workspace must be non-null and 256-byte aligned");
+    Layout L = make_layout(ctx->n, ctx->n_saved_cap, ctx->max_rhs, ctx->prec);
+    if (bytes < L.total)
+        return fail(ctx, FTK_ENOMEM, "workspace too small: need " + std::to_string(L.total));
+    ctx->ws = (char *)dev_ptr;
+    ctx->ws_bytes = bytes;
+    ctx->L = L;
+    ctx->have_state = 0;
+    ctx->n_saved = 0;
+    ctx->k = 0;
+    ctx->slot_valid.assign(ctx->max_rhs, 0);
+    CK(cudaMemsetAsync(ctx->dsmall, 0, sizeof(Small), ctx->stream));
+    return FTK_OK;
+}
+
+ftk_status ftk_tpq_init(ftk_ctx *ctx, uint64_t seed, uint32_t sample, double ell) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if ((s = check_ell(ctx, ell))) return s;
+    ctx->ell = ell;
+    InitArgs ia{};
+    ia.dim = ctx->dim;
+    ia.seed = seed;
+    ia.sample = sample;
+    ia.partials = (double *)wsp(ctx, ctx->L.partials);
+    ia.counter = &ctx->dsmall->counters[0];
+    ia.result = ctx->dsmall->op_dots;
+    ia.tpq = &ctx->dsmall->tpq;
+    TpqState h{};
+    h.ell = ell;
+    h.n_sites = ctx->n;
+    CK(cudaMemcpyAsync(&ctx->dsmall->tpq, &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
+    LAUNCH(launch_init_state(FTK_FP64, wsp(ctx, ctx->L.psi[0]), ia, vec_grid(ctx, ctx->dim), ctx->stream));
+    ctx->k = 0;
+    ctx->n_saved = 0;
+    ctx->have_state = 1;
+    return FTK_OK;
+}
+
+static ftk_status load_vector(ftk_ctx *ctx, const double *v, int is_device, void *dst, int prec) {
+    // stage as double2 in the Krylov region (3 * max_rhs vectors >= 16 B / amplitude)
+    void *stage = wsp(ctx, ctx->L.kry[0]);
+    const size_t bytes = ctx->dim * 16;
+    if (prec == FTK_FP64) {
+        CK(cudaMemcpyAsync(dst, v, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           ctx->stream));
+        return FTK_OK;
+    }
+    CK(cudaMemcpyAsync(stage, v, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       ctx->stream));
+    LAUNCH(launch_convert_in(prec, stage, dst, ctx->dim, vec_grid(ctx, ctx->dim), ctx->stream));
+    return FTK_OK;
+}
+
+ftk_status ftk_set_state(ftk_ctx *ctx, const double *v, int32_t is_device, double ell) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (!v) return fail(ctx, FTK_EINVAL, "null vector");
+    if ((s = check_ell(ctx, ell))) return s;
+    ctx->ell = ell;
+    TpqState h{};
+    h.ell = ell;
+    h.n_sites = ctx->n;
+    CK(cudaMemcpyAsync(&ctx->dsmall->tpq, &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
+    if ((s = load_vector(ctx, v, is_device, wsp(ctx, ctx->L.psi[0]), FTK_FP64))) return s;
+    InitArgs ia{};
+    ia.dim = ctx->dim;
+    ia.partials = (double *)wsp(ctx, ctx->L.partials);
+    ia.counter = &ctx->dsmall->counters[0];
+    ia.result = ctx->dsmall->op_dots;
+    ia.tpq = &ctx->dsmall->tpq;
+    LAUNCH(launch_norm(FTK_FP64, wsp(ctx, ctx->L.psi[0]), ia, vec_grid(ctx, ctx->dim), ctx->stream));
+    ctx->k = 0;
+    ctx->n_saved = 0;
+    ctx->have_state = 1;
+    if (!is_device) CK(cudaStreamSynchronize(ctx->stream));
+    return FTK_OK;
+}
+
+ftk_status ftk_tpq_step(ftk_ctx *ctx, int32_t n_steps, int32_t save_every, double *u_out,
+                        double *logQ_out, double *h2_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (!ctx->have_state) return fail(ctx, FTK_EBUSY, "no TPQ state: call ftk_tpq_init first");
+    Plan *pl64 = nullptr;
+    if ((s = get_plan(ctx, FTK_FP64, 1, &pl64))) return s;
+    if (n_steps < 0 || save_every < 1) return fail(ctx, FTK_EINVAL, "bad n_steps / save_every");
+    if (ctx->n_saved > 0 && save_every != ctx->save_every)
+        return fail(ctx, FTK_EINVAL, "save_every must not change between calls");
+    ctx->save_every = save_every;
+    const int k0 = ctx->k;
+    int need_saved = ctx->n_saved;
+    for (int k = k0; k < k0 + n_steps; ++k) need_saved += (k % save_every == 0);
+    if (need_saved > ctx->n_saved_cap)
+        return fail(ctx, FTK_ENOMEM, "more shells than n_saved (" + std::to_string(ctx->n_saved_cap) + ")");
+    if ((s = ensure_stats(ctx, k0 + n_steps))) return s;
+    EpiArgs ea{};
+    ea.scale = &ctx->dsmall->tpq.scale;
+    ea.ell = ctx->ell;
+    ea.inv_n = 1.0 / ctx->n;
+    ea.partials = (double *)wsp(ctx, ctx->L.partials);
+    ea.counter = &ctx->dsmall->counters[1];
+    ea.result = ctx->dsmall->op_dots;
+    ea.tpq = &ctx->dsmall->tpq;
+    ea.stat_u = stat_u(ctx);
+    ea.stat_logq = stat_lq(ctx);
+    ea.stat_h2 = stat_h2(ctx);
+    for (int k = k0; k < k0 + n_steps; ++k) {
+        void *cur = wsp(ctx, ctx->L.psi[k & 1]);
+        void *nxt = wsp(ctx, ctx->L.psi[(k + 1) & 1]);
+        if (k % save_every == 0) {
+            const int sidx = ctx->n_saved;
+            void *dst = wsp(ctx, ctx->L.shells + ctx->L.vec_bytes * sidx);
+            if (ctx->prec == FTK_FP64)
+                CK(cudaMemcpyAsync(dst, cur, ctx->L.vec_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+            else
+                LAUNCH(launch_convert_in(ctx->prec, cur, dst, ctx->dim, vec_grid(ctx, ctx->dim), ctx->stream));
+            CK(cudaMemcpyAsync(ctx->shell_scale + sidx, &ctx->dsmall->tpq.scale, sizeof(double),
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+            ctx->shell_step.resize(sidx + 1);
+            ctx->shell_step[sidx] = k;
+            ctx->n_saved = sidx + 1;
+        }
+        if ((s = run_hv(ctx, FTK_FP64, 1, EPI_TPQ, cur, nxt, ea))) return s;
+        ctx->k = k + 1;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (n_steps > 0) {
+        if (u_out) CK(cudaMemcpy(u_out, stat_u(ctx) + k0, n_steps * sizeof(double), cudaMemcpyDeviceToHost));
+        if (logQ_out) CK(cudaMemcpy(logQ_out, stat_lq(ctx) + k0, n_steps * sizeof(double), cudaMemcpyDeviceToHost));
+        if (h2_out) CK(cudaMemcpy(h2_out, stat_h2(ctx) + k0, n_steps * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return FTK_OK;
+}
+
+ftk_status ftk_shells(const ftk_ctx *cctx, int32_t *n_out, int32_t *step_out, double *energy_out) {
+    ftk_ctx *ctx = const_cast<ftk_ctx *>(cctx);
+    if (!ctx) return FTK_EINVAL;
+    if (n_out) *n_out = ctx->n_saved;
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int s = 0; s < ctx->n_saved; ++s) {
+        if (step_out) step_out[s] = ctx->shell_step[s];
+        if (energy_out) {
+            double u = 0;
+            CK(cudaMemcpy(&u, stat_u(ctx) + ctx->shell_step[s], sizeof u, cudaMemcpyDeviceToHost));
+            energy_out[s] = u * ctx->n;
+        }
+    }
+    return FTK_OK;
+}
+
+ftk_status ftk_apply_op(ftk_ctx *ctx, int32_t shell, int32_t gamma, const double q[2], int32_t slot) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (shell < 0 || shell >= ctx->n_saved) return fail(ctx, FTK_EINVAL, "shell index out of range");
+    if (gamma < 0 || gamma > 2 || !q) return fail(ctx, FTK_EINVAL, "bad gamma or q");
+    if (slot < 0 || slot >= ctx->max_rhs) return fail(ctx, FTK_EINVAL, "rhs slot out of range");
+    if (ctx->shell_step[shell] >= ctx->k)
+        return fail(ctx, FTK_EBUSY, "shell statistics not computed yet (run one more TPQ step)");
+    OpArgs oa{};
+    oa.n_sites = ctx->n;
+    oa.gamma = gamma;
+    oa.dim = ctx->dim;
+    const double nrm = 1.0 / std::sqrt((double)ctx->n);
+    for (int l = 0; l < ctx->n; ++l) {
+        const double ph = q[0] * ctx->pos[2 * l] + q[1] * ctx->pos[2 * l + 1];
+        oa.f_re[l] = nrm * std::cos(ph);
+        oa.f_im[l] = nrm * std::sin(ph);
+    }
+    oa.scale = ctx->shell_scale + shell;
+    oa.partials = (double *)wsp(ctx, ctx->L.partials);
+    oa.counter = &ctx->dsmall->counters[2];
+    oa.result = ctx->dsmall->op_dots;
+    oa.energy_src = stat_u(ctx) + ctx->shell_step[shell];
+    oa.n_sites_d = ctx->n;
+    oa.slot_energy = ctx->slot_energy + slot;
+    oa.slot_norm2 = ctx->slot_norm2 + slot;
+    LAUNCH(launch_apply_op(ctx->prec, wsp(ctx, ctx->L.shells + ctx->L.vec_bytes * shell),
+                           wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * slot), oa, vec_grid(ctx, ctx->dim),
+                           ctx->stream));
+    ctx->slot_valid[slot] = 1;
+    return FTK_OK;
+}
+
+ftk_status ftk_set_probe(ftk_ctx *ctx, int32_t slot, const double *v, int32_t is_device, double energy) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (slot < 0 || slot >= ctx->max_rhs || !v) return fail(ctx, FTK_EINVAL, "bad slot or vector");
+    if ((s = load_vector(ctx, v, is_device, wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * slot), ctx->prec))) return s;
+    CK(cudaMemcpyAsync(ctx->slot_energy + slot, &energy, sizeof energy, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->slot_valid[slot] = 1;
+    return FTK_OK;
+}
+
+// One blocked COCG iteration on the context stream (no host sync):
+// H R_cur -> W (+mu), seed scalars, shift recurrences, R_prev <- update.
+static ftk_status cocg_iteration(ftk_ctx *ctx, int B, void *rcur, void *rprev, void *w,
+                                 const EpiArgs &ea, const SeedArgs &sa, const ShiftArgs &sh,
+                                 UpdArgs ua) {
+    ftk_status s = run_hv(ctx, ctx->prec, B, EPI_COCG, rcur, w, ea);
+    if (s) return s;
+    LAUNCH(launch_cocg_seed(sa, ctx->stream));
+    LAUNCH(launch_cocg_shift(sh, B, ctx->stream));
+    ua.mode = 1;
+    LAUNCH(launch_cocg_update(ctx->prec, B, rcur, w, rprev, ua, vec_grid(ctx, ctx->dim * B), ctx->stream));
+    return FTK_OK;
+}
+
+ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, const double *omega,
+                            int32_t n_omega, double eta, double tol, int32_t max_iter, double *G_out,
+                            int32_t *iters_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (!slots || n_rhs < 1 || n_rhs > ctx->max_rhs || !omega || n_omega < 1 || n_omega > FTK_MAX_OMEGA ||
+        !G_out || !(eta > 0) || !(tol > 0) || max_iter < 1)
+        return fail(ctx, FTK_EINVAL, "bad shifted COCG arguments");
+    for (int j = 0; j < n_rhs; ++j)
+        if (slots[j] < 0 || slots[j] >= ctx->max_rhs || !ctx->slot_valid[slots[j]])
+            return fail(ctx, FTK_EINVAL, "rhs slot not loaded");
+    int B = 1;
+    while (B < n_rhs) B <<= 1;
+    if (B > ctx->max_rhs) {
+        // block wider than the Krylov region: split into two halves
+        const int h = n_rhs / 2;
+        ftk_status s1 = ftk_shifted_cocg(ctx, slots, h, omega, n_omega, eta, tol, max_iter, G_out, iters_out);
+        if (s1 != FTK_OK && s1 != FTK_ENOCONV && s1 != FTK_EBREAKDOWN) return s1;
+        ftk_status s2 = ftk_shifted_cocg(ctx, slots + h, n_rhs - h, omega, n_omega, eta, tol, max_iter,
+                                         G_out + size_t(2) * h * n_omega, iters_out ? iters_out + h : nullptr);
+        if (s2 != FTK_OK && s2 != FTK_ENOCONV && s2 != FTK_EBREAKDOWN) return s2;
+        return s1 != FTK_OK ? s1 : s2;
+    }
+    Plan *pl = nullptr;
+    if ((s = get_plan(ctx, ctx->prec, B, &pl))) return s;
+    Small *d = ctx->dsmall;
+    // per-RHS seed scalars: z_s = E_j + omega[mid] + i eta
+    std::vector<double> e(n_rhs);
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int j = 0; j < n_rhs; ++j)
+        CK(cudaMemcpy(&e[j], ctx->slot_energy + slots[j], sizeof(double), cudaMemcpyDeviceToHost));
+    const int mid = n_omega / 2;
+    std::vector<CocgSeed> seeds(B);
+    for (int j = 0; j < B; ++j) {
+        memset(&seeds[j], 0, sizeof(CocgSeed));
+        const int jj = j < n_rhs ? j : 0;          // padding lanes repeat RHS 0
+        seeds[j].e0 = e[jj];
+        seeds[j].zs_re = e[jj] + omega[mid];
+        seeds[j].zs_im = eta;
+        seeds[j].alpha_re = 1.0;
+    }
+    CK(cudaMemcpyAsync(d->seed, seeds.data(), sizeof(CocgSeed) * B, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(d->inv_pi_max, 0, sizeof(d->inv_pi_max), ctx->stream));
+    CK(cudaMemsetAsync(&d->all_done, 0, sizeof(int), ctx->stream));
+    double *om = (double *)wsp(ctx, ctx->L.omega);
+    CK(cudaMemcpyAsync(om, omega, sizeof(double) * n_omega, cudaMemcpyHostToDevice, ctx->stream));
+    // shift arrays: pi_prev = pi_cur = 1, p~ = 0, G = 0
+    const size_t sa_elems = size_t(B) * n_omega;
+    dcx *sbase = (dcx *)wsp(ctx, ctx->L.shift);
+    dcx *pi_prev = sbase, *pi_cur = sbase + sa_elems, *ptil = sbase + 2 * sa_elems, *G = sbase + 3 * sa_elems;
+    {
+        std::vector<double> ones(2 * sa_elems, 0.0);
+        for (size_t i = 0; i < sa_elems; ++i) ones[2 * i] = 1.0;
+        CK(cudaMemcpyAsync(pi_prev, ones.data(), sa_elems * 16, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(pi_cur, ones.data(), sa_elems * 16, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemsetAsync(ptil, 0, sa_elems * 16 * 3, ctx->stream));   // p~, G, frozen
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    void *kr[3] = {wsp(ctx, ctx->L.kry[0]), wsp(ctx, ctx->L.kry[1]), wsp(ctx, ctx->L.kry[2])};
+    void *rcur = kr[0], *rprev = kr[1], *w = kr[2];
+
+    UpdArgs ua{};
+    ua.dim = ctx->dim;
+    for (int j = 0; j < B; ++j) {
+        const int jj = j < n_rhs ? j : 0;
+        ua.lambda[j] = wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * slots[jj]);
+    }
+    ua.seed = d->seed;
+    ua.partials = (double *)wsp(ctx, ctx->L.partials);
+    ua.counter = &d->counters[3];
+    ua.result = d->upd_dots;
+    ua.all_done = &d->all_done;
+    EpiArgs ea{};
+    ea.partials = (double *)wsp(ctx, ctx->L.partials);
+    ea.counter = &d->counters[4];
+    ea.result = d->hv_dots;
+    ea.all_done = &d->all_done;
+    SeedArgs sa{};
+    sa.n_rhs = B;
+    sa.max_iter = max_iter;
+    sa.tol = tol;
+    sa.seed = d->seed;
+    sa.upd = d->upd_dots;
+    sa.hv = d->hv_dots;
+    sa.inv_pi_max = d->inv_pi_max;
+    sa.all_done = &d->all_done;
+    ShiftArgs sh{};
+    sh.n_omega = n_omega;
+    sh.seed_idx = mid;
+    sh.omega = om;
+    sh.seed = d->seed;
+    sh.pi_prev = pi_prev; sh.pi_cur = pi_cur; sh.ptil = ptil; sh.G = G;
+    sh.inv_pi_max = d->inv_pi_max;
+    sh.frozen = reinterpret_cast<int *>(sbase + 4 * sa_elems);
+    sh.tol = tol;
+
+    // r_0 = lambda (+ dots); r_{-1} = 0 so that c_0 r_{-1} is exactly zero
+    CK(cudaMemsetAsync(rprev, 0, ctx->L.vec_bytes * B, ctx->stream));
+    ua.mode = 0;
+    LAUNCH(launch_cocg_update(ctx->prec, B, nullptr, nullptr, rcur, ua, vec_grid(ctx, ctx->dim * B), ctx->stream));
+
+    // Capture two iterations (buffer roles return to the start) in a graph.
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const int64_t l0 = ctx->launches;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ftk_status cs = cocg_iteration(ctx, B, rcur, rprev, w, ea, sa, sh, ua);
+    if (cs == FTK_OK) cs = cocg_iteration(ctx, B, rprev, rcur, w, ea, sa, sh, ua);
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (cs != FTK_OK) { if (graph) cudaGraphDestroy(graph); return cs; }
+    CK(ce);
+    const int64_t per_graph = ctx->launches - l0;
+    ctx->launches = l0;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ce);
+    int done = 0, it = 0;
+    const int chunk = 16;   // graph launches between host checks (32 iterations)
+    ftk_status result = FTK_OK;
+    while (!done) {
+        for (int g = 0; g < chunk && it <= max_iter + 2; ++g, it += 2) {
+            ce = cudaGraphLaunch(exec, ctx->stream);
+            if (ce != cudaSuccess) break;
+            ctx->launches += per_graph;
+        }
+        if (ce != cudaSuccess) break;
+        ce = cudaMemcpyAsync(&done, &d->all_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+        if (ce != cudaSuccess) break;
+        if (it > max_iter + 2) break;
+    }
+    cudaGraphExecDestroy(exec);
+    CK(ce);
+    // results
+    std::vector<CocgSeed> out(B);
+    CK(cudaMemcpy(out.data(), d->seed, sizeof(CocgSeed) * B, cudaMemcpyDeviceToHost));
+    std::vector<double> g(2 * sa_elems);
+    CK(cudaMemcpy(g.data(), G, sa_elems * 16, cudaMemcpyDeviceToHost));
+    for (int j = 0; j < n_rhs; ++j) {
+        memcpy(G_out + size_t(2) * j * n_omega, g.data() + size_t(2) * j * n_omega, sizeof(double) * 2 * n_omega);
+        if (iters_out) iters_out[j] = out[j].iters;
+        if (out[j].done == 2 && result == FTK_OK) result = FTK_EBREAKDOWN;
+        if ((out[j].done == 4 || out[j].done == 0) && result == FTK_OK) result = FTK_ENOCONV;
+    }
+    if (result == FTK_ENOCONV) ctx->err = "shifted COCG reached max_iter";
+    if (result == FTK_EBREAKDOWN) ctx->err = "shifted COCG breakdown";
+    return result;
+}
+
+ftk_status ftk_spectrum(ftk_ctx *ctx, const double *Gh, int32_t n_shell, int32_t n_omega, const double *T,
+                        int32_t n_T, double *S_out, int32_t *trunc_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (!Gh || !T || !S_out || n_shell < 1 || n_shell > ctx->n_saved || n_shell > 1024 || n_omega < 1 ||
+        n_omega > FTK_MAX_OMEGA || n_T < 1 || n_T > 1024)
+        return fail(ctx, FTK_EINVAL, "bad spectrum arguments");
+    for (int t = 0; t < n_T; ++t)
+        if (!(T[t] > 0)) return fail(ctx, FTK_EINVAL, "temperatures must be positive");
+    double *gb = (double *)wsp(ctx, ctx->L.gbuf);
+    double *tb = (double *)wsp(ctx, ctx->L.tbuf);
+    // S and trunc reuse the Krylov region as output staging
+    double *sb = (double *)wsp(ctx, ctx->L.kry[0]);
+    int *trb = (int *)(sb + size_t(n_T) * n_omega);
+    if (ctx->L.vec_bytes * ctx->max_rhs < size_t(n_T) * n_omega * 8 + n_T * 4 + 16)
+        return fail(ctx, FTK_ENOMEM, "Krylov region too small to stage the spectrum");
+    CK(cudaMemcpyAsync(gb, Gh, size_t(16) * n_shell * n_omega, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(tb, T, sizeof(double) * n_T, cudaMemcpyHostToDevice, ctx->stream));
+    SpecArgs sp{};
+    sp.n_sites_i = ctx->n;
+    sp.n_sites = ctx->n;
+    sp.ell = ctx->ell;
+    sp.n_steps = ctx->k;
+    sp.save_every = ctx->save_every;
+    sp.n_shell = n_shell;
+    sp.n_omega = n_omega;
+    sp.u = stat_u(ctx);
+    sp.logq = stat_lq(ctx);
+    sp.G = gb;
+    sp.T = tb;
+    sp.S = sb;
+    sp.trunc = trb;
+    LAUNCH(launch_spectrum(sp, n_T, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(S_out, sb, sizeof(double) * n_T * n_omega, cudaMemcpyDeviceToHost));
+    std::vector<int> tr(n_T);
+    CK(cudaMemcpy(tr.data(), trb, sizeof(int) * n_T, cudaMemcpyDeviceToHost));
+    int any = 0;
+    for (int t = 0; t < n_T; ++t) {
+        if (trunc_out) trunc_out[t] = tr[t];
+        any |= tr[t];
+    }
+    return any ? FTK_ETRUNC : FTK_OK;
+}
+
+ftk_status ftk_hv(ftk_ctx *ctx, const void *v_dev, void *out_dev, int32_t n_rhs) {
+    if (!ctx) return FTK_EINVAL;
+    if (!v_dev || !out_dev || v_dev == out_dev) return fail(ctx, FTK_EINVAL, "bad vectors");
+    if ((reinterpret_cast<uintptr_t>(v_dev) | reinterpret_cast<uintptr_t>(out_dev)) & 15)
+        return fail(ctx, FTK_EINVAL, "vectors must be 16-byte aligned");
+    if (n_rhs < 1 || n_rhs > FTK_MAX_RHS || (n_rhs & (n_rhs - 1)))
+        return fail(ctx, FTK_EINVAL, "n_rhs must be a power of two <= 32");
+    EpiArgs ea{};
+    return run_hv(ctx, ctx->prec, n_rhs, EPI_PLAIN, v_dev, out_dev, ea);
+}
+
+ftk_status ftk_get_vector(ftk_ctx *ctx, int32_t which, double *host_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (!host_out) return fail(ctx, FTK_EINVAL, "null output");
+    const void *src = nullptr;
+    const double *scale = nullptr;
+    if (which == 0) {
+        if (!ctx->have_state) return fail(ctx, FTK_EBUSY, "no TPQ state");
+        src = wsp(ctx, ctx->L.psi[ctx->k & 1]);
+        scale = &ctx->dsmall->tpq.scale;
+    } else if (which > 0) {
+        const int sh = which - 1;
+        if (sh >= ctx->n_saved) return fail(ctx, FTK_EINVAL, "no such shell");
+        src = wsp(ctx, ctx->L.shells + ctx->L.vec_bytes * sh);
+        scale = ctx->shell_scale + sh;
+    } else {
+        const int sl = -1 - which;
+        if (sl >= ctx->max_rhs || !ctx->slot_valid[sl]) return fail(ctx, FTK_EINVAL, "no such probe");
+        src = wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * sl);
+    }
+    void *stage = wsp(ctx, ctx->L.kry[0]);
+    LAUNCH(launch_convert_out(which == 0 ? FTK_FP64 : ctx->prec, src, stage, ctx->dim, scale,
+                              vec_grid(ctx, ctx->dim), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(host_out, stage, ctx->dim * 16, cudaMemcpyDeviceToHost));
+    return FTK_OK;
+}
+
+ftk_status ftk_plan_info(const ftk_ctx *cctx, int32_t *n_passes, int32_t *tile_bits) {
+    ftk_ctx *ctx = const_cast<ftk_ctx *>(cctx);
+    if (!ctx) return FTK_EINVAL;
+    Plan *pl = nullptr;
+    ftk_status s = get_plan(ctx, ctx->prec, 1, &pl);
+    if (s) return s;
+    if (n_passes) *n_passes = (int)pl->passes.size();
+    if (tile_bits) *tile_bits = pl->tile_bits;
+    return FTK_OK;
+}
+
+int64_t ftk_launch_count(const ftk_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+const char *ftk_last_error(const ftk_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+void ftk_destroy(ftk_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->dsmall) cudaFree(ctx->dsmall);
+    if (ctx->stats) cudaFree(ctx->stats);
+    if (ctx->shell_scale) cudaFree(ctx->shell_scale);
+    if (ctx->slot_energy) cudaFree(ctx->slot_energy);
+    if (ctx->slot_norm2) cudaFree(ctx->slot_norm2);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+}  // extern "C"

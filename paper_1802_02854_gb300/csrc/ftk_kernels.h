@@ -1,0 +1,111 @@
+// Launch arguments and launchers of the FTKomega kernels (host <-> device).
+#pragma once
+#include "ftk_common.cuh"
+
+namespace ftk {
+
+enum { EPI_PLAIN = 0, EPI_TPQ = 1, EPI_COCG = 2 };
+
+struct EpiArgs {
+    const double *scale;     // TPQ: device s_k
+    double ell, inv_n;       // TPQ: l, 1/N
+    double *partials;        // [grid][nd] scratch
+    unsigned int *counter;   // last-block ticket (reset by the last block)
+    double *result;          // reduced dots [nd]
+    TpqState *tpq;           // TPQ state (updated by the last block)
+    double *stat_u, *stat_logq, *stat_h2;   // TPQ statistics arrays [k]
+    const int *all_done;     // COCG: skip when every RHS finished (or NULL)
+};
+
+struct UpdArgs {
+    int mode;                // 0: r = lambda, 1: 3-term update
+    uint64_t dim;
+    const void *lambda[FTK_MAX_RHS];
+    const CocgSeed *seed;
+    double *partials;
+    unsigned int *counter;
+    double *result;          // [B][FTK_UPD_DOTS]
+    const int *all_done;
+};
+
+struct SeedArgs {
+    int n_rhs;
+    int max_iter;
+    double tol;
+    CocgSeed *seed;
+    const double *upd;       // [B][FTK_UPD_DOTS]
+    const double *hv;        // [B][FTK_HV_DOTS]
+    double *inv_pi_max;      // [2][FTK_MAX_RHS] parity double buffer
+    int *all_done;
+};
+
+struct ShiftArgs {
+    int n_omega;
+    int seed_idx;
+    const double *omega;     // [n_omega]
+    const CocgSeed *seed;
+    struct dcx *pi_prev, *pi_cur, *ptil, *G;   // [B][n_omega]
+    double *inv_pi_max;      // [2][FTK_MAX_RHS]
+    int *frozen;             // [B][n_omega] converged shifts
+    double tol;
+};
+
+struct OpArgs {
+    int n_sites;
+    int gamma;
+    uint64_t dim;
+    double f_re[FTK_MAX_SITES], f_im[FTK_MAX_SITES];   // N^{-1/2} exp(i q.R_l)
+    const double *scale;     // device scale of the source vector
+    double *partials;
+    unsigned int *counter;
+    double *result;
+    const double *energy_src; // device u_k of the source shell (or NULL)
+    double n_sites_d;
+    double energy_val;
+    double *slot_energy;     // device shift origin of the slot
+    double *slot_norm2;      // device ||lambda||^2
+};
+
+struct InitArgs {
+    uint64_t dim;
+    uint64_t seed;
+    uint32_t sample;
+    double *partials;
+    unsigned int *counter;
+    double *result;
+    TpqState *tpq;
+};
+
+struct SpecArgs {
+    int n_sites_i;
+    double n_sites;
+    double ell;
+    int n_steps;             // K: statistics for k = 0..K-1
+    int save_every;
+    int n_shell;
+    int n_omega;
+    const double *u, *logq;  // [K]
+    const double *G;         // [n_shell][n_omega][2]
+    const double *T;         // [n_T]
+    double *S;               // [n_T][n_omega]
+    int *trunc;              // [n_T]
+};
+
+cudaError_t init_kernel_attributes();
+cudaError_t launch_hv_pass(int prec, int B, int epi, const void *in, void *out, const PassDesc &pd,
+                           const EpiArgs &ea, int grid, int threads, size_t smem, cudaStream_t st);
+size_t hv_smem_bytes(int prec, int B, int tile_bits, int chunk_bits, int threads);
+cudaError_t launch_cocg_update(int prec, int B, const void *rcur, const void *w, void *rprev_new,
+                               const UpdArgs &ua, int grid, cudaStream_t st);
+cudaError_t launch_cocg_seed(const SeedArgs &sa, cudaStream_t st);
+cudaError_t launch_cocg_shift(const ShiftArgs &sh, int n_rhs, cudaStream_t st);
+cudaError_t launch_apply_op(int prec, const void *psi, void *lam, const OpArgs &oa, int grid,
+                            cudaStream_t st);
+cudaError_t launch_init_state(int prec, void *v, const InitArgs &ia, int grid, cudaStream_t st);
+cudaError_t launch_norm(int prec, const void *v, const InitArgs &ia, int grid, cudaStream_t st);
+cudaError_t launch_convert_in(int prec, const void *src, void *dst, uint64_t n, int grid, cudaStream_t st);
+cudaError_t launch_convert_out(int prec, const void *src, void *dst, uint64_t n, const double *scale,
+                               int grid, cudaStream_t st);
+cudaError_t launch_spectrum(const SpecArgs &sp, int n_T, cudaStream_t st);
+
+}  // namespace ftk

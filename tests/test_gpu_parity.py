@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C-ABI) with the oracle, element by
+element on the same seeded inputs. GPU only.
+
+Bars: H.v <= 1e-12 (FP64) / 1e-6 (FP32) relative 2-norm; spectra <= 1e-8
+(FP64) / 1e-5 (FP32) relative 2-norm against the oracle's estimator."""
+import numpy as np
+import pytest
+
+from ftk_inputs import named, honeycomb, random_state, random_vectors, omega_grid, relabel
+from oracle import dense, sparse
+
+pytestmark = pytest.mark.gpu
+
+TOL_HV = {"fp64": 1e-12, "fp32": 1e-6}
+TOL_S = {"fp64": 1e-8, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def ftk():
+    import torch
+    from paper_1802_02854_gb300 import build
+    assert torch.cuda.is_available()
+    build.build()
+    import paper_1802_02854_gb300 as m
+    m.lib()
+    return m
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _gpu_hv(ftk, cl, K, J, prec, vs, tile_bits=0):
+    import torch
+    b = vs.shape[0]
+    ctx = ftk.Context(cl, K, J, prec, max_rhs=b, tile_bits=tile_bits)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    v = torch.from_numpy(np.ascontiguousarray(vs.T)).to(dt).cuda().contiguous()
+    out = ctx.hv(v if b > 1 else v[:, 0].contiguous())
+    torch.cuda.synchronize()
+    res = out.cpu().numpy().astype(np.complex128).reshape(cl.dim, b).T
+    info = ctx.plan_info()
+    ctx.close()
+    return res, info
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,tile_bits,B", [(2, 0, 1), (8, 0, 1), (12, 6, 1), (12, 0, 4), (14, 7, 2),
+                                           (16, 0, 1), (16, 9, 8), (18, 0, 1), (12, 5, 32)])
+@pytest.mark.parametrize("K,J", [(-1.0, 0.1), (-1.0, 0.0), (0.0, 1.0)])
+def test_hv_parity(ftk, prec, n, tile_bits, B, K, J):
+    cl = named(n) if n != 14 else honeycomb((1, 7))
+    vs = random_vectors(n, B, 1000 + n + B)
+    got, (n_pass, tb) = _gpu_hv(ftk, cl, K, J, prec, vs, tile_bits)
+    if tile_bits and tile_bits < n:
+        assert n_pass >= 2
+    for j in range(B):
+        ref = sparse.hv(cl, K, J, vs[j])
+        assert rel(got[j], ref) <= TOL_HV[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_hv_full_size_n24(ftk, prec):
+    """Full-size 24-site cluster in the bench's launch configuration, every
+    element compared with the oracle."""
+    cl = named(24)
+    vs = random_vectors(24, 1, 77)
+    got, (n_pass, _) = _gpu_hv(ftk, cl, -1.0, 0.1, prec, vs)
+    ref = sparse.hv(cl, -1.0, 0.1, vs[0])
+    assert rel(got[0], ref) <= TOL_HV[prec]
+
+
+def test_hv_relabelled_sites(ftk):
+    """Any site labelling gives the same operator (the bits are relabelled)."""
+    cl = named(12)
+    perm = np.random.default_rng(3).permutation(12)
+    cl2 = relabel(cl, perm)
+    vs = random_vectors(12, 1, 5)
+    got, _ = _gpu_hv(ftk, cl2, -1.0, 0.1, "fp64", vs, 6)
+    assert rel(got[0], sparse.hv(cl2, -1.0, 0.1, vs[0])) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_init_state_philox(ftk, prec):
+    """Device Philox4x32-10 + Box-Muller state == the oracle's generator."""
+    cl = named(12)
+    ctx = ftk.Context(cl, -1.0, 0.1, prec)
+    ctx.tpq_init(20240611, 3, 0.5)
+    got = ctx.get_vector(0)
+    ref = sparse.gaussian_state(12, 20240611, 3)
+    assert rel(got, ref) <= (1e-13 if prec == "fp64" else 1e-7)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tpq_parity(ftk, prec):
+    cl = named(12)
+    K, J, ell = -1.0, 0.1, 0.5
+    psi0 = random_state(12, 9)
+    ctx = ftk.Context(cl, K, J, prec, n_saved=8, tile_bits=7)
+    ctx.set_state(psi0, ell)
+    u, lq, h2 = ctx.tpq_step(41, 10)
+    shells, ur, lqr, h2r = sparse.tpq(cl, K, J, psi0, ell, 41, 10)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert np.abs(u - ur).max() < tol
+    assert np.abs(lq - lqr).max() < tol * 50
+    assert np.abs(h2 - h2r).max() < tol * 100
+    steps, energies = ctx.shells()
+    assert steps.tolist() == [0, 10, 20, 30, 40]
+    assert np.abs(energies - 12 * ur[steps]).max() < tol * 12
+    for s in range(len(steps)):
+        assert rel(ctx.get_vector(1 + s), shells[s]) < (1e-12 if prec == "fp64" else 1e-5)
+    ctx.close()
+
+
+def test_tpq_rejects_small_ell(ftk):
+    cl = named(8)
+    ctx = ftk.Context(cl, -1.0, 0.1, "fp64")
+    with pytest.raises(ftk.FtkError) as e:
+        ctx.set_state(random_state(8, 1), 0.3)
+    assert e.value.status == ftk.FTK_EINVAL
+    ctx.close()
+
+
+@pytest.mark.parametrize("gamma", [0, 1, 2])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_op_parity(ftk, gamma, prec):
+    cl = named(12)
+    psi0 = random_state(12, 4)
+    ctx = ftk.Context(cl, -1.0, 0.1, prec, max_rhs=2, n_saved=2)
+    ctx.set_state(psi0, 0.5)
+    ctx.tpq_step(1, 1)
+    for qi in (0, 2):
+        ctx.apply_op(0, gamma, cl.momenta[qi], 1)
+        got = ctx.get_vector(-2)
+        ref = sparse.apply_op(cl, gamma, cl.momenta[qi], psi0)
+        assert rel(got, ref) <= (1e-13 if prec == "fp64" else 1e-6)
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_cocg_parity(ftk, n):
+    cl = named(n)
+    K, J = -1.0, 0.1
+    psi0 = random_state(n, 13)
+    ctx = ftk.Context(cl, K, J, "fp64", max_rhs=1, n_saved=1)
+    ctx.set_state(psi0, 0.5)
+    ctx.tpq_step(1, 1)
+    steps, en = ctx.shells()
+    q = cl.momenta[1]
+    ctx.apply_op(0, 2, q, 0)
+    omega = omega_grid(-2, 2, 100)
+    eta = 0.05
+    G, it, _ = ctx.shifted_cocg([0], omega, eta, tol=1e-10, max_iter=5000)
+    lam = sparse.apply_op(cl, 2, q, psi0)
+    z = en[0] + omega + 1j * eta
+    Gr, itr, _, st = sparse.cocg(cl, K, J, lam, z[50], z, 1e-10, 5000)
+    assert st == 0
+    assert abs(int(it[0]) - itr) <= max(3, itr // 50)
+    assert np.abs(G[0] - Gr).max() <= 1e-8 * np.abs(Gr).max()
+    ctx.close()
+
+
+def test_blocked_equals_single(ftk):
+    """Three RHS in one block (padded to 4) == three single-RHS solves."""
+    cl = named(12)
+    psi0 = random_state(12, 21)
+    ctx = ftk.Context(cl, -1.0, 0.1, "fp64", max_rhs=4, n_saved=1)
+    ctx.set_state(psi0, 0.5)
+    ctx.tpq_step(1, 1)
+    omega = omega_grid(-2, 2, 77)
+    for slot, (g, qi) in enumerate([(0, 0), (1, 1), (2, 3)]):
+        ctx.apply_op(0, g, cl.momenta[qi], slot)
+    Gb, itb, _ = ctx.shifted_cocg([0, 1, 2], omega, 0.04, tol=1e-10, max_iter=5000)
+    for slot in range(3):
+        Gs, its, _ = ctx.shifted_cocg([slot], omega, 0.04, tol=1e-10, max_iter=5000)
+        assert np.abs(Gb[slot] - Gs[0]).max() <= 1e-10 * np.abs(Gs[0]).max()
+        assert abs(int(itb[slot]) - int(its[0])) <= max(3, int(its[0]) // 50)
+    ctx.close()
+
+
+def test_cocg_deterministic(ftk):
+    cl = named(12)
+    ctx = ftk.Context(cl, -1.0, 0.1, "fp64", max_rhs=2, n_saved=1)
+    ctx.set_state(random_state(12, 2), 0.5)
+    ctx.tpq_step(1, 1)
+    ctx.apply_op(0, 0, cl.momenta[1], 0)
+    ctx.apply_op(0, 1, cl.momenta[2], 1)
+    om = omega_grid(-1, 1, 300)
+    a, _, _ = ctx.shifted_cocg([0, 1], om, 0.05, tol=1e-8, max_iter=3000)
+    b, _, _ = ctx.shifted_cocg([0, 1], om, 0.05, tol=1e-8, max_iter=3000)
+    assert np.array_equal(a, b)
+    ctx.close()
+
+
+def test_cocg_edge_cases(ftk):
+    cl = named(8)
+    ctx = ftk.Context(cl, -1.0, 0.1, "fp64", max_rhs=2, n_saved=1)
+    ctx.set_state(random_state(8, 2), 0.5)
+    ctx.tpq_step(1, 1)
+    # zero probe: G == 0, no iterations
+    ctx.set_probe(0, np.zeros(256, dtype=np.complex128), -1.0)
+    G, it, st = ctx.shifted_cocg([0], omega_grid(-1, 1, 5), 0.05, tol=1e-8, max_iter=100)
+    assert np.all(G == 0) and it[0] == 0
+    # single shift, equal to the seed: plain resolvent
+    lam = random_state(8, 5)
+    ctx.set_probe(1, lam, 0.25)
+    G, it, st = ctx.shifted_cocg([1], np.array([0.1]), 0.07, tol=1e-12, max_iter=500)
+    h = dense.hamiltonian(cl, -1.0, 0.1)
+    x = np.linalg.solve((0.35 + 0.07j) * np.eye(256) - h, lam)
+    assert abs(G[0, 0] - np.vdot(lam, x)) <= 1e-10 * abs(np.vdot(lam, x))
+    # max_iter reached: FTK_ENOCONV, G still written
+    G, it, st = ctx.shifted_cocg([1], omega_grid(-2, 2, 9), 0.01, tol=1e-14, max_iter=3, allow_noconv=True)
+    assert st == ftk.FTK_ENOCONV and it[0] == 3 and np.all(np.isfinite(G))
+    ctx.close()
+
+
+def test_dimer_closed_form_spectrum(ftk):
+    """1x1 torus: H = (K+3J) S_A.S_B; at q with exp(i q.d_z) = -1 the exact
+    Green's function of lambda = S^z_q psi is a sum of two poles."""
+    cl = honeycomb((1, 1))
+    K, J = -1.0, 0.2
+    ctx = ftk.Context(cl, K, J, "fp64", max_rhs=1, n_saved=1)
+    psi = random_state(2, 3)
+    ctx.set_state(psi, 0.8)
+    ctx.tpq_step(1, 1)
+    ctx.apply_op(0, 2, [np.pi, 0.0], 0)
+    om = omega_grid(-2, 2, 33)
+    G, it, _ = ctx.shifted_cocg([0], om, 0.05, tol=1e-12, max_iter=50)
+    lam = ctx.get_vector(-1)
+    dg = dense.Diag(cl, K, J)
+    e0 = ctx.shells()[1][0]
+    c = dg.V.T @ lam
+    want = (np.abs(c) ** 2 / (e0 + om[:, None] + 0.05j - dg.E[None, :])).sum(axis=1)
+    assert np.abs(G[0] - want).max() <= 1e-12 * np.abs(want).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_pipeline_vs_dense_estimator(ftk, prec):
+    """mTPQ -> S^z_q probes -> shifted COCG -> reweighting, N = 12 (2x3,
+    K = -1, J = 0.1), against O-DENSE-EST on the same seeded state."""
+    cl = named(12)
+    K, J, ell, eta = -1.0, 0.1, 0.5, 0.02
+    n_steps, se = 61, 20
+    psi0 = random_state(12, 2024)
+    omega = omega_grid(-2, 2, 256)
+    T = np.array([0.5, 1.0, 2.0])
+    dg = dense.Diag(cl, K, J)
+    ctx = ftk.Context(cl, K, J, prec, max_rhs=4, n_saved=4)
+    ctx.set_state(psi0, ell)
+    ctx.tpq_step(n_steps, se)
+    steps, en = ctx.shells()
+    tol = 1e-11 if prec == "fp64" else 1e-6
+    for qi in (1, 3):
+        q = cl.momenta[qi]
+        for s in range(len(steps)):
+            ctx.apply_op(s, 2, q, s)
+        G, it, _ = ctx.shifted_cocg(list(range(len(steps))), omega, eta, tol=tol, max_iter=6000,
+                                    allow_noconv=(prec == "fp32"))
+        S, tr = ctx.spectrum(G, T)
+        ref = dense.dense_estimator(dg, psi0, ell, n_steps, se, 2, q, omega, eta, T)
+        assert rel(G.ravel(), ref["G"].ravel()) <= TOL_S[prec]
+        assert rel(S, ref["S"]) <= TOL_S[prec]
+        assert tr.tolist() == ref["trunc"].astype(int).tolist()
+    ctx.close()

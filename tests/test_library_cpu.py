@@ -1,0 +1,66 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every symbol include/ftk.h declares, sizes workspaces and rejects bad
+arguments before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ftk():
+    from paper_1802_02854_gb300 import build
+    build.build()
+    import paper_1802_02854_gb300 as m
+    return m
+
+
+def _header_symbols():
+    src = open(os.path.join(ROOT, "include", "ftk.h")).read()
+    return sorted(set(re.findall(r"\b(ftk_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(ftk):
+    declared = _header_symbols()
+    assert set(declared) == set(ftk.EXPORTS)
+    lib = C.CDLL(ftk.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_footprint_layout(ftk):
+    f64 = ftk.ftk_footprint(12, 4, 2, ftk.FTK_FP64)
+    f32 = ftk.ftk_footprint(12, 4, 2, ftk.FTK_FP32)
+    d = 1 << 12
+    # 2 TPQ + 4 shells + 2 probes + 3*2 Krylov vectors
+    assert f64 >= 14 * d * 16 and f32 >= 14 * d * 8
+    assert f64 - f32 >= 14 * d * 8 - 14 * 256
+    assert ftk.ftk_footprint(31, 1, 1, 0) == 0
+    assert ftk.ftk_footprint(12, 0, 1, 0) == 0
+    assert ftk.ftk_footprint(12, 1, 33, 0) == 0
+    assert ftk.ftk_footprint(12, 1, 1, 7) == 0
+
+
+@pytest.mark.parametrize("bad", ["site", "self", "gamma", "prec", "rhs"])
+def test_create_rejects_bad_arguments(ftk, bad):
+    from ftk_inputs import named
+    cl = named(8)
+    bonds = cl.bonds.copy()
+    kw = dict(precision=ftk.FTK_FP64, max_rhs=1, n_saved=1)
+    if bad == "site":
+        bonds[0, 1] = 8
+    elif bad == "self":
+        bonds[0, 1] = bonds[0, 0]
+    elif bad == "gamma":
+        bonds[0, 2] = 3
+    elif bad == "prec":
+        kw["precision"] = 5
+    elif bad == "rhs":
+        kw["max_rhs"] = 64
+    with pytest.raises(ftk.FtkError) as e:
+        ftk.ftk_create(cl.n_sites, cl.pos, bonds, -1.0, 0.1, **kw)
+    assert e.value.status == ftk.FTK_EINVAL
