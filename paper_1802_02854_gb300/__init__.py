@@ -28,7 +28,7 @@ STATUS_NAMES = ["FTK_OK", "FTK_EINVAL", "FTK_ENOMEM", "FTK_ECUDA", "FTK_ENOCONV"
 EXPORTS = ["ftk_footprint", "ftk_create", "ftk_bind_workspace", "ftk_tpq_init", "ftk_set_state",
            "ftk_tpq_step", "ftk_shells", "ftk_apply_op", "ftk_set_probe", "ftk_shifted_cocg",
            "ftk_spectrum", "ftk_hv", "ftk_get_vector", "ftk_plan_info", "ftk_launch_count",
-           "ftk_last_error", "ftk_destroy"]
+           "ftk_last_error", "ftk_destroy", "ftk_tpq_step_noalloc"]
 
 
 class FtkError(RuntimeError):
@@ -86,6 +86,7 @@ def lib() -> C.CDLL:
     L.ftk_last_error.restype = C.c_char_p
     L.ftk_destroy.argtypes = [vp]
     L.ftk_destroy.restype = None
+    L.ftk_tpq_step_noalloc.argtypes = [i32, C.POINTER(_Bond), i32, dbl, dbl, dbl, vp, vp, pd, vp]
     for name in EXPORTS:
         if name not in ("ftk_footprint", "ftk_launch_count", "ftk_last_error", "ftk_destroy"):
             getattr(L, name).restype = C.c_int
@@ -221,6 +222,18 @@ def ftk_launch_count(ctx):
 def ftk_destroy(ctx):
     if ctx:
         lib().ftk_destroy(ctx)
+
+
+def ftk_tpq_step_noalloc(n_sites, bonds, K, J, ell, psi_ptr, out_ptr, stream=None):
+    """One allocation-free mTPQ step on caller device vectors (FP64).
+    Returns (u, <H^2>, q); out = (l - H/N) psi unnormalised."""
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 3)
+    barr = (_Bond * len(bonds))(*[_Bond(int(i), int(j), int(g)) for i, j, g in bonds])
+    st = np.zeros(3)
+    _check(None, lib().ftk_tpq_step_noalloc(int(n_sites), barr, len(bonds), float(K), float(J), float(ell),
+                                            C.c_void_p(psi_ptr), C.c_void_p(out_ptr), _dp(st),
+                                            C.c_void_p(int(stream) if stream else 0)))
+    return float(st[0]), float(st[1]), float(st[2])
 
 
 # ----------------------------------------------------------------- wrapper

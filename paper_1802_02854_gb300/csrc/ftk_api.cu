@@ -3,6 +3,7 @@
 #include "../../include/ftk.h"
 #include "ftk_common.cuh"
 #include "ftk_kernels.h"
+#include "ftk_plan.h"
 
 #include <algorithm>
 #include <cmath>
@@ -20,7 +21,7 @@ namespace {
 const size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-struct Bond { int i, j, g; double par, anti, dg; };
+struct Bond { int i, j, g; };
 
 // Workspace regions (bytes from the workspace base).
 struct Layout {
@@ -74,6 +75,10 @@ struct Plan {
 
 }  // namespace
 
+namespace ftk {
+void set_thread_error(const char *msg);
+}
+
 struct ftk_ctx {
     int n = 0, nb = 0, prec = 0, max_rhs = 1, n_saved_cap = 1, tile_bits_req = 0;
     uint64_t dim = 0;
@@ -104,7 +109,7 @@ struct ftk_ctx {
 
 namespace {
 
-thread_local std::string g_create_err;   // message of the last failed ftk_create
+thread_local std::string g_create_err;   // last context-free failure on this thread
 
 ftk_status fail(ftk_ctx *c, ftk_status s, const std::string &m) {
     if (c) c->err = m;
@@ -127,96 +132,20 @@ ftk_status fail(ftk_ctx *c, ftk_status s, const std::string &m) {
 
 int elem_bytes(int prec) { return prec == FTK_FP64 ? 16 : 8; }
 
-// Greedy cover of the bonds by tile bit sets. The first pass takes the low
-// tile_bits sites (good when sites are labelled so that neighbours have close
-// numbers); each later pass keeps the chunk_bits lowest sites (coalescing)
-// and adds, one at a time, the site that completes most remaining bonds.
+}  // namespace
+
+void ftk::set_thread_error(const char *msg) { g_create_err = msg; }
+
+namespace {
+
 bool plan_passes(ftk_ctx *ctx, int prec, int B, int tile_bits, Plan &pl) {
-    const int n = ctx->n;
-    const int es = elem_bytes(prec);
-    int c = 0;
-    while (c < n && (size_t(1) << c) * B * es < 256) ++c;   // >= 256 B contiguous runs
-    int b = std::min(tile_bits, n);
-    if (b < n && c > b - 2) c = std::max(0, b - 2);   // later passes need >= 2 free tile bits
-    if (c > b) c = b;
-    pl.tile_bits = b;
-    pl.chunk_bits = c;
-    pl.passes.clear();
-    std::vector<int> remaining(ctx->nb);
-    for (int q = 0; q < ctx->nb; ++q) remaining[q] = q;
-    std::vector<int> T;
-    for (int s = 0; s < b; ++s) T.push_back(s);
-    for (int guard = 0; guard < 64; ++guard) {
-        std::vector<char> in_t(n, 0);
-        for (int s : T) in_t[s] = 1;
-        std::vector<int> take, rest;
-        for (int q : remaining) {
-            const Bond &bd = ctx->bonds[q];
-            if (in_t[bd.i] && in_t[bd.j] && (int)take.size() < FTK_MAX_PASS_BONDS) take.push_back(q);
-            else rest.push_back(q);
-        }
-        if (take.empty() && !remaining.empty()) return false;
-        std::sort(T.begin(), T.end());
-        PassDesc pd;
-        memset(&pd, 0, sizeof pd);
-        pd.n_sites = n;
-        pd.tile_bits = b;
-        pd.chunk_bits = c;
-        pd.n_free = n - b;
-        int tpos[FTK_MAX_SITES];
-        for (int s = 0; s < n; ++s) tpos[s] = -1;
-        for (int k = 0; k < b; ++k) { pd.tile_pos[k] = T[k]; tpos[T[k]] = k; }
-        int f = 0;
-        for (int s = 0; s < n; ++s) if (!in_t[s]) pd.free_pos[f++] = s;
-        pd.n_bonds = (int)take.size();
-        for (int l = 0; l < pd.n_bonds; ++l) {
-            const Bond &bd = ctx->bonds[take[l]];
-            pd.bi[l] = tpos[bd.i];
-            pd.bj[l] = tpos[bd.j];
-            pd.par[l] = bd.par;
-            pd.anti[l] = bd.anti;
-            pd.par_f[l] = (float)bd.par;
-            pd.anti_f[l] = (float)bd.anti;
-            pd.dgc[l] = bd.g == 2 ? 1 : 0;
-        }
-        pd.dgv[0] = ctx->J / 4;
-        pd.dgv[1] = (ctx->J + ctx->K) / 4;
-        pd.dgv_f[0] = (float)pd.dgv[0];
-        pd.dgv_f[1] = (float)pd.dgv[1];
-        pl.passes.push_back(pd);
-        remaining = rest;
-        if (remaining.empty()) break;
-        // next tile set
-        T.clear();
-        std::vector<char> in2(n, 0);
-        for (int s = 0; s < c; ++s) { T.push_back(s); in2[s] = 1; }
-        while ((int)T.size() < b) {
-            int best = -1;
-            long best_score = -1;
-            for (int s = 0; s < n; ++s) {
-                if (in2[s]) continue;
-                long done = 0, touch = 0;
-                for (int q : remaining) {
-                    const Bond &bd = ctx->bonds[q];
-                    const bool hi = bd.i == s || bd.j == s;
-                    if (!hi) continue;
-                    ++touch;
-                    const int other = bd.i == s ? bd.j : bd.i;
-                    if (in2[other]) ++done;
-                }
-                const long score = done * 1000 + touch;
-                if (score > best_score) { best_score = score; best = s; }
-            }
-            T.push_back(best);
-            in2[best] = 1;
-        }
-    }
-    if (!remaining.empty()) return false;
-    const int np = (int)pl.passes.size();
-    for (int p = 0; p < np; ++p) {
-        pl.passes[p].first = p == 0;
-        pl.passes[p].last = p == np - 1;
-    }
+    PlanBond pb[2 * FTK_MAX_PASS_BONDS];
+    for (int q = 0; q < ctx->nb; ++q) pb[q] = {ctx->bonds[q].i, ctx->bonds[q].j, ctx->bonds[q].g};
+    PassDesc pd[FTK_MAX_PASSES];
+    const int np = plan_hv_passes(ctx->n, pb, ctx->nb, ctx->K, ctx->J, elem_bytes(prec), B, tile_bits, pd,
+                                  FTK_MAX_PASSES, &pl.tile_bits, &pl.chunk_bits);
+    if (np == 0) return false;
+    pl.passes.assign(pd, pd + np);
     return true;
 }
 
@@ -350,21 +279,7 @@ ftk_status ftk_create(const ftk_lattice *lat, const ftk_bond *bonds, int32_t n_b
     ctx->n_saved_cap = opts->n_saved;
     ctx->tile_bits_req = opts->tile_bits;
     ctx->pos.assign(lat->pos, lat->pos + 2 * n);
-    // Matrix elements of h_b = J S_i.S_j + K S^g_i S^g_j on the S^z basis:
-    //   S^x S^x |x> = 1/4 |x'>, S^y S^y |x> = -s_i s_j / 4 |x'>, S^z S^z = s_i s_j / 4
-    // with x' = x ^ 2^i ^ 2^j, so for parallel (p) / antiparallel (a) spins
-    //   x-bond: p K/4,  a K/4 + J/2;  y-bond: p -K/4, a K/4 + J/2;  z-bond: p 0, a J/2
-    // and the diagonal is +dg (p) / -dg (a) with dg = J/4 (x, y), (J + K)/4 (z).
-    for (int q = 0; q < n_bonds; ++q) {
-        Bond bd;
-        bd.i = bonds[q].i;
-        bd.j = bonds[q].j;
-        bd.g = bonds[q].gamma;
-        if (bd.g == 0) { bd.par = K / 4; bd.anti = K / 4 + J / 2; bd.dg = J / 4; }
-        else if (bd.g == 1) { bd.par = -K / 4; bd.anti = K / 4 + J / 2; bd.dg = J / 4; }
-        else { bd.par = 0; bd.anti = J / 2; bd.dg = (J + K) / 4; }
-        ctx->bonds.push_back(bd);
-    }
+    for (int q = 0; q < n_bonds; ++q) ctx->bonds.push_back({bonds[q].i, bonds[q].j, bonds[q].gamma});
     // l_min: the bond block has eigenvalues (J+K)/4 (x2), (J-K)/4, -(3J+K)/4
     const double lmax = std::max({(J + K) / 4, (J - K) / 4, -(3 * J + K) / 4});
     ctx->ell_min = n_bonds * lmax / n;

@@ -92,6 +92,7 @@ struct SpecArgs {
 };
 
 cudaError_t init_kernel_attributes();
+void set_thread_error(const char *msg);   // message for ftk_last_error(NULL)
 cudaError_t launch_hv_pass(int prec, int B, int epi, const void *in, void *out, const PassDesc &pd,
                            const EpiArgs &ea, int grid, int threads, size_t smem, cudaStream_t st);
 size_t hv_smem_bytes(int prec, int B, int tile_bits, int chunk_bits, int threads);
