@@ -178,7 +178,7 @@ def run_gpu(args):
 
     # dominant kernel: the blocked H.V of the COCG solve (same plan, same B),
     # timed alone with CUDA events on the context stream
-    v = torch.randn(dim, n_rhs, dtype=torch.complex128, device="cuda")
+    v = torch.randn(n_rhs, dim, dtype=torch.complex128, device="cuda")
     out = torch.empty_like(v)
     torch.cuda.synchronize()
     for _ in range(3):
@@ -319,7 +319,7 @@ def run_hv_only(args):
     prec = args.hv_prec
     ctx = ftk.Context(cl, K_COUPLING, J_COUPLING, prec, max_rhs=args.hv_rhs)
     dt = torch.complex128 if prec == "fp64" else torch.complex64
-    v = torch.randn(cl.dim, args.hv_rhs, dtype=dt, device="cuda")
+    v = torch.randn(args.hv_rhs, cl.dim, dtype=dt, device="cuda")
     out = torch.empty_like(v)
     torch.cuda.synchronize()
     for _ in range(args.hv_reps):

@@ -168,8 +168,8 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *rhs_slots, int32_t n_rh
 ftk_status ftk_spectrum(ftk_ctx *ctx, const double *G, int32_t n_shell, int32_t n_omega,
                         const double *T, int32_t n_T, double *S_out, int32_t *trunc_out);
 
-/* out = H v for n_rhs interleaved vectors (layout [2^N][n_rhs] complex in the
- * context precision). v and out are device pointers, must not overlap, and
+/* out = H v for n_rhs vectors stored one after the other (layout
+ * [n_rhs][2^N] complex in the context precision: vector j at offset j 2^N). v and out are device pointers, must not overlap, and
  * need 16-byte alignment. The product of Sec. IV.A's cost unit ("a Lanczos
  * step"); exposed for tests and the bandwidth metric. Asynchronous. */
 ftk_status ftk_hv(ftk_ctx *ctx, const void *v_dev, void *out_dev, int32_t n_rhs);
@@ -181,6 +181,17 @@ ftk_status ftk_get_vector(ftk_ctx *ctx, int32_t which, double *host_out);
 
 /* Number of H.v passes the plan uses, and the tile bits. */
 ftk_status ftk_plan_info(const ftk_ctx *ctx, int32_t *n_passes, int32_t *tile_bits);
+
+/* Site relabelling that lets H.v run in fewer tiled passes (the layout
+ * choice of Sec. IV.A's Hamiltonian-vector product on this hardware: the
+ * chunk sites, i.e. the lowest index bits, sit in every tile). Host only, no
+ * device work. bonds as in ftk_create; precision and n_rhs select the tile
+ * shape (tile_bits 0 = the default). perm_out (host, n_sites ints) receives
+ * site l -> new label perm_out[l]; relabel the sites (and their positions)
+ * before ftk_create. n_passes_out (may be NULL) receives the pass count.
+ * FTK_EINVAL on bad arguments (message via ftk_last_error(NULL)). */
+ftk_status ftk_suggest_order(int32_t n_sites, const ftk_bond *bonds, int32_t n_bonds, int32_t precision,
+                             int32_t n_rhs, int32_t tile_bits, int32_t *perm_out, int32_t *n_passes_out);
 
 /* Kernel launches issued by this context since creation (for accounting). */
 int64_t ftk_launch_count(const ftk_ctx *ctx);

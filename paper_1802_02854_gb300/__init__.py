@@ -28,7 +28,7 @@ STATUS_NAMES = ["FTK_OK", "FTK_EINVAL", "FTK_ENOMEM", "FTK_ECUDA", "FTK_ENOCONV"
 EXPORTS = ["ftk_footprint", "ftk_create", "ftk_bind_workspace", "ftk_tpq_init", "ftk_set_state",
            "ftk_tpq_step", "ftk_shells", "ftk_apply_op", "ftk_set_probe", "ftk_shifted_cocg",
            "ftk_spectrum", "ftk_hv", "ftk_get_vector", "ftk_plan_info", "ftk_launch_count",
-           "ftk_last_error", "ftk_destroy", "ftk_tpq_step_noalloc"]
+           "ftk_last_error", "ftk_destroy", "ftk_tpq_step_noalloc", "ftk_suggest_order"]
 
 
 class FtkError(RuntimeError):
@@ -87,6 +87,7 @@ def lib() -> C.CDLL:
     L.ftk_destroy.argtypes = [vp]
     L.ftk_destroy.restype = None
     L.ftk_tpq_step_noalloc.argtypes = [i32, C.POINTER(_Bond), i32, dbl, dbl, dbl, vp, vp, pd, vp]
+    L.ftk_suggest_order.argtypes = [i32, C.POINTER(_Bond), i32, i32, i32, i32, pi, pi]
     for name in EXPORTS:
         if name not in ("ftk_footprint", "ftk_launch_count", "ftk_last_error", "ftk_destroy"):
             getattr(L, name).restype = C.c_int
@@ -236,6 +237,18 @@ def ftk_tpq_step_noalloc(n_sites, bonds, K, J, ell, psi_ptr, out_ptr, stream=Non
     return float(st[0]), float(st[1]), float(st[2])
 
 
+def ftk_suggest_order(n_sites, bonds, precision=FTK_FP64, n_rhs=1, tile_bits=0):
+    """Site relabelling for fewer H.v passes: returns (perm, n_passes) with
+    site l -> new label perm[l] (apply with ftk_inputs.relabel)."""
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 3)
+    barr = (_Bond * len(bonds))(*[_Bond(int(i), int(j), int(g)) for i, j, g in bonds])
+    perm = np.zeros(n_sites, dtype=np.int32)
+    npass = C.c_int32()
+    _check(None, lib().ftk_suggest_order(int(n_sites), barr, len(bonds), int(precision), int(n_rhs),
+                                         int(tile_bits), _ip(perm), C.byref(npass)))
+    return perm.astype(np.int64), npass.value
+
+
 # ----------------------------------------------------------------- wrapper
 class Context:
     """A context plus the torch device workspace it runs in.
@@ -289,9 +302,10 @@ class Context:
         return ftk_spectrum(self.handle, G, T)
 
     def hv(self, v, out=None):
-        """v: torch tensor [dim] or [dim, B] of complex128/complex64 on cuda."""
+        """v: torch tensor [dim] or [B, dim] (B vectors, one after the other)
+        of complex128/complex64 on cuda."""
         torch = self.torch
-        n_rhs = 1 if v.dim() == 1 else v.shape[1]
+        n_rhs = 1 if v.dim() == 1 else v.shape[0]
         if out is None:
             out = torch.empty_like(v)
         cur = torch.cuda.current_stream()

@@ -142,9 +142,11 @@ bool plan_passes(ftk_ctx *ctx, int prec, int B, int tile_bits, Plan &pl) {
     PlanBond pb[2 * FTK_MAX_PASS_BONDS];
     for (int q = 0; q < ctx->nb; ++q) pb[q] = {ctx->bonds[q].i, ctx->bonds[q].j, ctx->bonds[q].g};
     PassDesc pd[FTK_MAX_PASSES];
-    const int np = plan_hv_passes(ctx->n, pb, ctx->nb, ctx->K, ctx->J, elem_bytes(prec), B, tile_bits, pd,
-                                  FTK_MAX_PASSES, &pl.tile_bits, &pl.chunk_bits);
+    const int np = plan_hv_passes(ctx->n, pb, ctx->nb, ctx->K, ctx->J, elem_bytes(prec), std::min(B, hv_max_b(prec)),
+                                  tile_bits, pd, FTK_MAX_PASSES, &pl.tile_bits, &pl.chunk_bits);
     if (np == 0) return false;
+    for (int p = 0; p < np; ++p)
+        if (!hv_layout_pass(pd[p], prec, B)) return false;
     pl.passes.assign(pd, pd + np);
     return true;
 }
@@ -152,29 +154,20 @@ bool plan_passes(ftk_ctx *ctx, int prec, int B, int tile_bits, Plan &pl) {
 ftk_status get_plan(ftk_ctx *ctx, int prec, int B, Plan **out) {
     auto it = ctx->plans.find(prec * 64 + B);
     if (it != ctx->plans.end()) { *out = &it->second; return FTK_OK; }
-    const int es = elem_bytes(prec);
-    int tb = ctx->tile_bits_req;
-    if (tb <= 0) {
-        // default: ~96 KB of tile per CTA (two CTAs per SM), at most 14 bits
-        tb = 0;
-        while ((size_t(2) << tb) * B * es <= size_t(96) << 10 && tb < 14) ++tb;
-    }
+    // default: the largest tile (two 64 KB shared-memory buffers per CTA)
+    const int tb_max = hv_max_tile_bits(prec, B);
+    int tb = ctx->tile_bits_req > 0 ? std::min(ctx->tile_bits_req, tb_max) : tb_max;
     tb = std::max(2, std::min(tb, ctx->n));
-    while (tb > 2 && (size_t(1) << tb) * B * es > (size_t(200) << 10)) --tb;   // shared-memory cap
     Plan pl;
     if (!plan_passes(ctx, prec, B, tb, pl))
         return fail(ctx, FTK_EINVAL, "H.v pass planning failed (tile too small for the bond list)");
-    pl.threads = std::min(B >= 8 ? 256 : 512, std::max(32, (1 << pl.tile_bits)));
-    pl.smem = hv_smem_bytes(prec, B, pl.tile_bits, pl.chunk_bits, pl.threads);
+    pl.threads = hv_threads(pl.passes[0]);
+    pl.smem = hv_smem_bytes(prec, B, pl.passes[0]);
     if (pl.smem > (size_t(227) << 10))
         return fail(ctx, FTK_EINVAL, "tile does not fit in shared memory");
-    int per_sm = 1;
-    // occupancy: shared memory bound (228 KB per SM incl. 1 KB per CTA reserve)
-    per_sm = std::max(1, (int)((size_t(228) << 10) / (pl.smem + 1024)));
-    per_sm = std::min(per_sm, 2048 / pl.threads);
-    const long n_tiles = 1L << (ctx->n - pl.tile_bits);
-    pl.grid = (int)std::min<long>(n_tiles, (long)per_sm * ctx->n_sm);
-    if (pl.grid < 1) pl.grid = 1;
+    // cap of the persistent grid (the launcher trims it to the resident CTAs);
+    // the reduction partials hold 4 MB
+    pl.grid = 8 * ctx->n_sm;
     auto res = ctx->plans.emplace(prec * 64 + B, pl);
     *out = &res.first->second;
     return FTK_OK;
@@ -197,8 +190,7 @@ ftk_status run_hv(ftk_ctx *ctx, int prec, int B, int epi, const void *in, void *
     const int np = (int)pl->passes.size();
     for (int p = 0; p < np; ++p) {
         const int e = (p == np - 1) ? epi : EPI_PLAIN;
-        LAUNCH(launch_hv_pass(prec, B, e, in, out, pl->passes[p], ea, pl->grid, pl->threads,
-                              pl->smem, ctx->stream));
+        LAUNCH(launch_hv_pass(prec, B, e, in, out, pl->passes[p], ea, pl->grid, ctx->stream));
     }
     return FTK_OK;
 }
@@ -523,7 +515,7 @@ static ftk_status cocg_iteration(ftk_ctx *ctx, int B, void *rcur, void *rprev, v
     LAUNCH(launch_cocg_seed(sa, ctx->stream));
     LAUNCH(launch_cocg_shift(sh, B, ctx->stream));
     ua.mode = 1;
-    LAUNCH(launch_cocg_update(ctx->prec, B, rcur, w, rprev, ua, vec_grid(ctx, ctx->dim * B), ctx->stream));
+    LAUNCH(launch_cocg_update(ctx->prec, B, rcur, w, rprev, ua, vec_grid(ctx, ctx->dim), ctx->stream));
     return FTK_OK;
 }
 
@@ -626,7 +618,7 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     // r_0 = lambda (+ dots); r_{-1} = 0 so that c_0 r_{-1} is exactly zero
     CK(cudaMemsetAsync(rprev, 0, ctx->L.vec_bytes * B, ctx->stream));
     ua.mode = 0;
-    LAUNCH(launch_cocg_update(ctx->prec, B, nullptr, nullptr, rcur, ua, vec_grid(ctx, ctx->dim * B), ctx->stream));
+    LAUNCH(launch_cocg_update(ctx->prec, B, nullptr, nullptr, rcur, ua, vec_grid(ctx, ctx->dim), ctx->stream));
 
     // Capture two iterations (buffer roles return to the start) in a graph.
     cudaGraph_t graph = nullptr;
@@ -768,6 +760,32 @@ ftk_status ftk_plan_info(const ftk_ctx *cctx, int32_t *n_passes, int32_t *tile_b
     if (s) return s;
     if (n_passes) *n_passes = (int)pl->passes.size();
     if (tile_bits) *tile_bits = pl->tile_bits;
+    return FTK_OK;
+}
+
+ftk_status ftk_suggest_order(int32_t n_sites, const ftk_bond *bonds, int32_t n_bonds, int32_t precision,
+                             int32_t n_rhs, int32_t tile_bits, int32_t *perm_out, int32_t *n_passes_out) {
+    if (n_sites < 2 || n_sites > FTK_MAX_SITES || !bonds || n_bonds < 1 || n_bonds > 2 * FTK_MAX_PASS_BONDS ||
+        (precision != FTK_FP64 && precision != FTK_FP32) || n_rhs < 1 || n_rhs > FTK_MAX_RHS ||
+        (n_rhs & (n_rhs - 1)) || !perm_out)
+        return fail(nullptr, FTK_EINVAL, "ftk_suggest_order: bad arguments");
+    PlanBond pb[2 * FTK_MAX_PASS_BONDS];
+    for (int q = 0; q < n_bonds; ++q) {
+        const ftk_bond &b = bonds[q];
+        if (b.i < 0 || b.j < 0 || b.i >= n_sites || b.j >= n_sites || b.i == b.j || b.gamma < 0 || b.gamma > 2)
+            return fail(nullptr, FTK_EINVAL, "ftk_suggest_order: bond out of range");
+        pb[q] = {b.i, b.j, b.gamma};
+    }
+    const int prec = precision == FTK_FP64 ? 0 : 1;
+    const int tb_max = hv_max_tile_bits(prec, n_rhs);
+    int tb = tile_bits > 0 ? std::min((int)tile_bits, tb_max) : tb_max;
+    tb = std::max(2, std::min(tb, (int)n_sites));
+    int perm[FTK_MAX_SITES];
+    const int np = plan_suggest_order(n_sites, pb, n_bonds, elem_bytes(prec), std::min((int)n_rhs, hv_max_b(prec)), tb,
+                                      perm);
+    if (np == 0) return fail(nullptr, FTK_EINVAL, "ftk_suggest_order: planning failed");
+    for (int s = 0; s < n_sites; ++s) perm_out[s] = perm[s];
+    if (n_passes_out) *n_passes_out = np;
     return FTK_OK;
 }
 

@@ -41,6 +41,20 @@ struct PassDesc {
     int32_t dgc[FTK_MAX_PASS_BONDS];
     double dgv[2];
     float dgv_f[2];
+    // Thread layout of the kernel (filled by hv_layout_pass): a CTA of
+    // 2^(tile_bits - le) threads, thread t owns the tile offsets t + 2^tb k
+    // for k < 2^le (tb = tile_bits - le), i.e. the top le offset bits are
+    // register bits. Bonds are ordered by group: the bonds of group g have
+    // the partner-thread mask grp_tmask[g] (the thread bits of their two
+    // sites) and occupy [grp_end[g-1], grp_end[g]); the last group has mask 0
+    // (partners held by the thread itself, and the diagonal). bcase encodes
+    // the register-bit part of the bond mask: 0 none, 1 + a one bit a,
+    // 5 + 4a + b two bits a < b.
+    int32_t le;
+    int32_t n_groups;
+    int32_t grp_tmask[FTK_MAX_PASS_BONDS + 1];
+    int32_t grp_end[FTK_MAX_PASS_BONDS + 1];
+    int8_t bcase[FTK_MAX_PASS_BONDS];
 };
 
 namespace ftk {

@@ -1,0 +1,119 @@
+// Device helpers shared by the FTKomega kernels: complex element types,
+// per-thread dot accumulators and deterministic block / last-block
+// reductions (fixed summation order, no floating-point atomics).
+#pragma once
+#include "ftk_common.cuh"
+
+namespace ftk {
+
+// ---------------------------------------------------------------- complex
+template <typename R> struct C2;
+template <> struct C2<double> { typedef double2 t; };
+template <> struct C2<float> { typedef float2 t; };
+
+template <typename R>
+__device__ __forceinline__ typename C2<R>::t mk(R a, R b) {
+    typename C2<R>::t z; z.x = a; z.y = b; return z;
+}
+
+// ------------------------------------------------ per-thread dot accumulator
+// double: plain sum. float: the product of two floats is split exactly into
+// p + e with an FMA (two-product) and both parts enter a Knuth two-sum
+// compensated float accumulator, converted to double once per thread.
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+    double s;
+    __device__ Acc() : s(0.0) {}
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ void fma2(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<float> {
+    float s, c;
+    __device__ Acc() : s(0.f), c(0.f) {}
+    __device__ __forceinline__ void add(float v) {
+        float t = s + v;
+        float bp = t - s;
+        float err = (s - (t - bp)) + (v - bp);
+        s = t;
+        c += err;
+    }
+    __device__ __forceinline__ void fma2(float a, float b) {
+        float p = a * b;
+        float e = fmaf(a, b, -p);
+        add(p);
+        c += e;
+    }
+    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
+// ---------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Reduce nd values per thread over the block (fixed order) into red[0..nd).
+// red must hold (blockDim/32) * nd doubles. Result valid in red[0..nd) after
+// the trailing __syncthreads.
+template <int ND>
+__device__ void block_reduce(double (&v)[ND], double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) v[d] = warp_sum(v[d]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) red[warp * ND + d] = v[d];
+    }
+    __syncthreads();
+    if (threadIdx.x < ND) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[w * ND + threadIdx.x];
+        red[threadIdx.x] = s;   // each thread reads column tid, writes slot tid
+    }
+    __syncthreads();
+}
+
+// Called by every thread of every CTA after it stored its ND partials at
+// partials[blockIdx.x * ND + d]. Returns true in the (unique) last CTA, after
+// it reduced all partials into out[0..ND) in a fixed order. Resets counter.
+template <int ND>
+__device__ bool last_block_reduce(const double *partials, unsigned int *counter, double *out,
+                                  double *red) {
+    __shared__ int am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    double v[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) v[d] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) v[d] += __ldcg(partials + (size_t)b * ND + d);
+    }
+    block_reduce<ND>(v, red);
+    if (threadIdx.x < ND) out[threadIdx.x] = red[threadIdx.x];
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+// Bond coefficients in the kernel's arithmetic type (no per-element conversion).
+template <typename R> struct Coef;
+template <> struct Coef<double> {
+    __device__ static __forceinline__ double par(const PassDesc &p, int l) { return p.par[l]; }
+    __device__ static __forceinline__ double anti(const PassDesc &p, int l) { return p.anti[l]; }
+    __device__ static __forceinline__ double dgv(const PassDesc &p, int c) { return p.dgv[c]; }
+};
+template <> struct Coef<float> {
+    __device__ static __forceinline__ float par(const PassDesc &p, int l) { return p.par_f[l]; }
+    __device__ static __forceinline__ float anti(const PassDesc &p, int l) { return p.anti_f[l]; }
+    __device__ static __forceinline__ float dgv(const PassDesc &p, int c) { return p.dgv_f[c]; }
+};
+
+}  // namespace ftk

@@ -1,0 +1,542 @@
+// One tiled pass of the matrix-free Kitaev-Heisenberg H.V on sm_103a (Sec.
+// IV.A: every method of the paper is costed in these products), with fused
+// epilogues for the mTPQ step (Appendix A) and the COCG mu = r^T H r dot.
+//
+// Data: B right-hand sides stored one after the other, element (x, j) at
+// j * ld + x (ld = 2^N). A CTA owns tiles of 2^b amplitudes: the offset bits of a tile
+// are the global bits pd.tile_pos[], the other bits (pd.free_pos[]) are fixed
+// by the tile index; the low offset bits are global bits 0..chunk-1 so every
+// tile is a set of >= 256-byte contiguous runs. Persistent CTAs loop over
+// tiles; the next tile is fetched with cp.async into the second of two
+// shared-memory buffers while the current one is processed.
+//
+// Thread layout: T = 2^tb threads, thread t owns the offsets o = t + T k,
+// k < E = 2^le (register bits = the top le offset bits), with accumulators
+// for all E x B amplitudes in registers. A bond (i, j) has partner o ^ m,
+// m = 2^bi | 2^bj: its thread part selects the partner thread t ^ tm, its
+// register part the partner register k ^ km. Bonds with the same tm form a
+// group: the thread reads the partner thread's E x B amplitudes once from
+// shared memory and applies every bond of the group from registers (the
+// coefficient choice par/anti is resolved once per thread and bond from the
+// thread bits, and at compile time from the register bits). The group with
+// tm = 0 holds the bonds between register sites, and the diagonal.
+#include "ftk_common.cuh"
+#include "ftk_device.cuh"
+#include "ftk_kernels.h"
+
+#include <algorithm>
+
+namespace ftk {
+
+// ------------------------------------------------------------ async copies
+__device__ __forceinline__ void cp_async_elem(float2 *dst, const float2 *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2 *dst, const double2 *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// -------------------------------------------------------- bond application
+template <int KA, int KB>
+struct KMask {
+    static constexpr int m = (KA >= 0 ? (1 << KA) : 0) | (KB >= 0 ? (1 << KB) : 0);
+};
+
+// acc[k] += c(k) P[k ^ km]: c = cs where the register bits of the bond are
+// parallel (k-parity 0), cf otherwise; k, k ^ km and the choice are
+// compile-time after unrolling.
+template <typename R, int B, int LE, int KA, int KB>
+__device__ __forceinline__ void bond_apply(R (&ar)[1 << LE][B], R (&ai)[1 << LE][B], const R (&pr)[1 << LE][B],
+                                           const R (&pi)[1 << LE][B], R cs, R cf) {
+    constexpr int E = 1 << LE;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int kpar = (KA >= 0 ? (k >> KA) & 1 : 0) ^ (KB >= 0 ? (k >> KB) & 1 : 0);
+        const int kp = k ^ KMask<KA, KB>::m;
+        const R c = kpar ? cf : cs;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            ar[k][j] = fma(c, pr[kp][j], ar[k][j]);
+            ai[k][j] = fma(c, pi[kp][j], ai[k][j]);
+        }
+    }
+}
+
+#define FTK_HV_CASE(ID, KA, KB)                                                                    \
+    case ID:                                                                                       \
+        if constexpr (KA < LE && KB < LE) bond_apply<R, B, LE, KA, KB>(ar, ai, pr, pim, cs, cf); \
+        break;
+
+template <typename R, int B, int LE, int EPI>
+__global__ void __launch_bounds__(512, 1)
+hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out, long long ld, const PassDesc pd,
+               const EpiArgs ea) {
+    typedef typename C2<R>::t cx;
+    constexpr int E = 1 << LE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (ea.all_done && *ea.all_done) return;
+    const int b = pd.tile_bits;
+    const int tb = b - LE;
+    const int tile_n = 1 << b;
+    const int T = 1 << tb;
+    const int t = threadIdx.x;
+    const bool act = t < T;
+    cx *buf0 = reinterpret_cast<cx *>(smem_raw);
+    cx *buf1 = buf0 + (size_t)tile_n * B;
+    cx *pbuf = buf1 + (size_t)tile_n * B;   // partial product of earlier passes
+    double *red = reinterpret_cast<double *>(pbuf + (size_t)tile_n * B);
+
+    // element offset of (offset t + T k, column j) from the tile base:
+    // st + ksp(k) + j ld, with st / ksp the global bits of the thread /
+    // register part (disjoint bits, so OR = sum)
+    uint64_t st = 0;
+    for (int q = 0; q < tb; ++q)
+        if ((t >> q) & 1) st |= 1ull << pd.tile_pos[q];
+    long long kofs[LE > 0 ? LE : 1];
+#pragma unroll
+    for (int q = 0; q < LE; ++q) kofs[q] = (long long)(1ull << pd.tile_pos[tb + q]);
+    auto eofs = [&](int k) -> long long {
+        long long v = (long long)st;
+#pragma unroll
+        for (int q = 0; q < LE; ++q)
+            if ((k >> q) & 1) v += kofs[q];
+        return v;
+    };
+    auto tile_ofs = [&](long tau) -> long long {
+        uint64_t v = 0;
+        for (int q = 0; q < pd.n_free; ++q)
+            if ((tau >> q) & 1) v |= 1ull << pd.free_pos[q];
+        return (long long)v;
+    };
+    // diagonal of this pass's bonds at the thread's offsets:
+    // +dg (parallel) / -dg (antiparallel), parity = thread part ^ register part
+    R dg[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) dg[k] = (R)0;
+    for (int l = 0; l < pd.n_bonds; ++l) {
+        const int m = (1 << pd.bi[l]) | (1 << pd.bj[l]);
+        const int pt = __popc(t & m & (T - 1)) & 1;
+        const int km = m >> tb;
+        const R d = Coef<R>::dgv(pd, pd.dgc[l]);
+#pragma unroll
+        for (int k = 0; k < E; ++k) dg[k] += ((pt ^ __popc(k & km)) & 1) ? -d : d;
+    }
+    const R scale = (EPI == EPI_TPQ) ? (R)(*ea.scale) : (R)1;
+    const R ell = (R)ea.ell, inv_n = (R)ea.inv_n;
+    constexpr int ND = (EPI == EPI_TPQ) ? 2 : (EPI == EPI_COCG ? 2 * B : 1);
+    Acc<R> dot[ND];
+    const bool first = pd.first != 0;
+
+    // async copy of a tile of `src` (the thread's own elements) into buf
+    auto issue = [&](const cx *src, long tau, cx *buf) {
+        if (act) {
+            const cx *g = src + tile_ofs(tau);
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const cx *gk = g + eofs(k);
+#pragma unroll
+                for (int j = 0; j < B; ++j) cp_async_elem(buf + (size_t)j * tile_n + t + T * k, gk + (size_t)j * ld);
+            }
+        }
+        cp_async_commit();
+    };
+    // Pipeline (commit order): v_0 [p_0] | per tile i: v_{i+1}, then after
+    // tile i's epilogue p_{i+1}. Each thread reads back only the partial
+    // elements it copied itself, so pbuf needs no block barrier.
+    const long n_tiles = 1L << pd.n_free;
+    long tau = blockIdx.x;
+    if (tau < n_tiles) {
+        issue(in, tau, buf0);
+        if (!first) issue(out, tau, pbuf);
+    }
+    for (int it = 0; tau < n_tiles; tau += gridDim.x, ++it) {
+        const cx *cur = (it & 1) ? buf1 : buf0;
+        cx *nxt = (it & 1) ? buf0 : buf1;
+        const long tn = tau + gridDim.x;
+        const bool more = tn < n_tiles;
+        if (more) issue(in, tn, nxt);
+        // v of this tile: everything but the newest one (first pass) or two groups
+        if (first) { if (more) cp_async_wait<1>(); else cp_async_wait<0>(); }
+        else { if (more) cp_async_wait<2>(); else cp_async_wait<1>(); }
+        __syncthreads();
+        if (act) {
+            R ar[E][B], ai[E][B];
+            R pr[E][B], pim[E][B];
+#pragma unroll
+            for (int k = 0; k < E; ++k)
+#pragma unroll
+                for (int j = 0; j < B; ++j) { ar[k][j] = (R)0; ai[k][j] = (R)0; }
+            int q = 0;
+            for (int g = 0; g < pd.n_groups; ++g) {
+                const int tm = pd.grp_tmask[g];
+                const cx *src = cur + (t ^ tm);
+#pragma unroll
+                for (int k = 0; k < E; ++k)
+#pragma unroll
+                    for (int j = 0; j < B; ++j) {
+                        const cx v = src[(size_t)j * tile_n + T * k];
+                        pr[k][j] = v.x;
+                        pim[k][j] = v.y;
+                    }
+                const int pt = __popc(t & tm) & 1;
+                for (const int end = pd.grp_end[g]; q < end; ++q) {
+                    const R par = Coef<R>::par(pd, q), anti = Coef<R>::anti(pd, q);
+                    const R cs = pt ? anti : par, cf = pt ? par : anti;
+                    switch (pd.bcase[q]) {
+                        FTK_HV_CASE(0, -1, -1)
+                        FTK_HV_CASE(1, 0, -1)
+                        FTK_HV_CASE(2, 1, -1)
+                        FTK_HV_CASE(3, 2, -1)
+                        FTK_HV_CASE(4, 3, -1)
+                        FTK_HV_CASE(5 + 0 * 4 + 1, 0, 1)
+                        FTK_HV_CASE(5 + 0 * 4 + 2, 0, 2)
+                        FTK_HV_CASE(5 + 0 * 4 + 3, 0, 3)
+                        FTK_HV_CASE(5 + 1 * 4 + 2, 1, 2)
+                        FTK_HV_CASE(5 + 1 * 4 + 3, 1, 3)
+                        FTK_HV_CASE(5 + 2 * 4 + 3, 2, 3)
+                        default: break;
+                    }
+                }
+            }
+            // the last group is the thread's own amplitudes: diagonal
+#pragma unroll
+            for (int k = 0; k < E; ++k)
+#pragma unroll
+                for (int j = 0; j < B; ++j) {
+                    ar[k][j] = fma(dg[k], pr[k][j], ar[k][j]);
+                    ai[k][j] = fma(dg[k], pim[k][j], ai[k][j]);
+                }
+            if (!first) {   // partial product of the earlier passes (own elements)
+                if (more) cp_async_wait<1>(); else cp_async_wait<0>();
+#pragma unroll
+                for (int k = 0; k < E; ++k)
+#pragma unroll
+                    for (int j = 0; j < B; ++j) {
+                        const cx p = pbuf[(size_t)j * tile_n + t + T * k];
+                        ar[k][j] += p.x;
+                        ai[k][j] += p.y;
+                    }
+            }
+            cx *o = out + tile_ofs(tau);
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                cx *ok = o + eofs(k);
+                if (!pd.last || EPI == EPI_PLAIN) {
+#pragma unroll
+                    for (int j = 0; j < B; ++j) ok[(size_t)j * ld] = mk<R>(ar[k][j], ai[k][j]);
+                } else if (EPI == EPI_TPQ) {
+                    // psi' = s (l v - H v / N);  <v|Hv>, |psi'|^2
+                    const R yr = scale * (ell * pr[k][0] - inv_n * ar[k][0]);
+                    const R yi = scale * (ell * pim[k][0] - inv_n * ai[k][0]);
+                    ok[0] = mk<R>(yr, yi);
+                    dot[0].fma2(pr[k][0], ar[k][0]);
+                    dot[0].fma2(pim[k][0], ai[k][0]);
+                    dot[1].fma2(yr, yr);
+                    dot[1].fma2(yi, yi);
+                } else {
+                    // W = H R;  mu_j = R_j^T W_j (bilinear)
+#pragma unroll
+                    for (int j = 0; j < B; ++j) {
+                        ok[(size_t)j * ld] = mk<R>(ar[k][j], ai[k][j]);
+                        dot[2 * j].fma2(pr[k][j], ar[k][j]);
+                        dot[2 * j].fma2(-pim[k][j], ai[k][j]);
+                        dot[2 * j + 1].fma2(pr[k][j], ai[k][j]);
+                        dot[2 * j + 1].fma2(pim[k][j], ar[k][j]);
+                    }
+                }
+            }
+        }
+        if (!first && more) issue(out, tn, pbuf);
+        __syncthreads();   // buffer `cur` is refilled two tiles later
+    }
+    cp_async_wait<0>();
+    if (EPI == EPI_PLAIN || !pd.last) return;
+
+    double v[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) v[d] = dot[d].get();
+    block_reduce<ND>(v, red);
+    if (threadIdx.x < ND) ea.partials[(size_t)blockIdx.x * ND + threadIdx.x] = red[threadIdx.x];
+    double *res = ea.result;
+    if (!last_block_reduce<ND>(ea.partials, ea.counter, res, red)) return;
+    if (EPI == EPI_TPQ && threadIdx.x == 0) {
+        // mTPQ statistics of step k (Appendix A): u_k = s^2 <v|Hv>/N,
+        // q_k = ||psi'||, <H^2>_k = N^2 (q^2 - l^2 + 2 l u_k)
+        TpqState *stt = ea.tpq;
+        const double s = stt->scale, n = stt->n_sites, l = stt->ell;
+        const double u = s * s * res[0] / n;
+        const double q2 = res[1];
+        const int k = stt->k;
+        ea.stat_u[k] = u;
+        ea.stat_logq[k] = stt->logQ;
+        ea.stat_h2[k] = n * n * (q2 - l * l + 2.0 * l * u);
+        stt->logQ += 0.5 * log(q2);
+        stt->scale = 1.0 / sqrt(q2);
+        stt->k = k + 1;
+    }
+}
+
+// ===================================================================== host
+// Register bits per thread: 16 (FP32) or 8 (FP64) amplitude-RHS pairs of
+// accumulators, i.e. le = log2(16 / B) or log2(8 / B). Right-hand-side blocks
+// wider than 8 are processed in column chunks of 8 (register budget).
+static int log2i(int v) {
+    int r = 0;
+    while ((1 << (r + 1)) <= v) ++r;
+    return r;
+}
+int hv_max_b(int prec) { (void)prec; return 8; }
+static int hv_le_default(int prec, int B) {
+    const int bc = std::min(B, hv_max_b(prec));
+    return std::max(0, (prec == 0 ? 3 : 4) - log2i(bc));
+}
+int hv_le(int prec, int B, int tile_bits, int chunk_bits) {
+    const int le = hv_le_default(prec, B);
+    if (tile_bits - le < 5 || tile_bits - le < chunk_bits) return 0;
+    return le;
+}
+// Largest tile: 64 KB (three such buffers per CTA: two for the input, one
+// for the partial product) and at most 512 threads.
+int hv_max_tile_bits(int prec, int B) {
+    const int bc = std::min(B, hv_max_b(prec));
+    const int es = prec == 0 ? 16 : 8;
+    int tb = 0;
+    while ((size_t(2) << tb) * bc * es <= (size_t(64) << 10)) ++tb;
+    return std::min(tb, 9 + hv_le_default(prec, B));
+}
+int hv_threads(const PassDesc &pd) {
+    const int t = 1 << (pd.tile_bits - pd.le);
+    return t < 32 ? 32 : t;
+}
+size_t hv_smem_bytes(int prec, int B, const PassDesc &pd) {
+    const int bc = std::min(B, hv_max_b(prec));
+    const size_t es = prec == 0 ? 16 : 8;
+    const int nd = std::max(2, 2 * bc);
+    return size_t(3) * ((size_t)1 << pd.tile_bits) * bc * es + (size_t)(hv_threads(pd) / 32) * nd * 8;
+}
+
+// Choose the register sites of a planned pass and order its bonds in groups.
+// The register sites are le of the non-chunk tile sites, picked to minimise
+// the number of groups (shared-memory reads per amplitude); the offset bits
+// are renumbered chunk sites, other thread sites, register sites.
+bool hv_layout_pass(PassDesc &pd, int prec, int B) {
+    const int b = pd.tile_bits, c = pd.chunk_bits, nb = pd.n_bonds;
+    const int le = hv_le(prec, B, b, c);
+    const int tb = b - le;
+    // choose the register positions among offset bits [c, b)
+    const int free_n = b - c;
+    int best_set = -1, best_groups = 1 << 30, best_rr = -1;
+    for (int set = 0; set < (1 << free_n); ++set) {
+        if (__builtin_popcount(set) != le) continue;
+        // bond masks with the chosen offset bits counted as register bits
+        int tms[FTK_MAX_PASS_BONDS + 1];
+        int ng = 0, rr = 0;
+        for (int l = 0; l < nb; ++l) {
+            int tm = 0, nreg = 0;
+            for (int side = 0; side < 2; ++side) {
+                const int o = side ? pd.bj[l] : pd.bi[l];
+                const bool reg = o >= c && ((set >> (o - c)) & 1);
+                if (reg) ++nreg;
+                else tm |= 1 << o;   // thread masks compared as sets of offset bits
+            }
+            if (nreg == 2) ++rr;
+            bool seen = tm == 0;
+            for (int g = 0; g < ng && !seen; ++g) seen = tms[g] == tm;
+            if (!seen) tms[ng++] = tm;
+        }
+        ++ng;   // the own group
+        if (ng < best_groups || (ng == best_groups && rr > best_rr)) {
+            best_groups = ng;
+            best_rr = rr;
+            best_set = set;
+        }
+        if (free_n > 20) break;
+    }
+    if (best_set < 0) return false;
+    // renumber offset bits: chunk bits, other thread bits, register bits
+    int newpos[FTK_MAX_TILE_BITS];
+    int nt = 0;
+    for (int o = 0; o < c; ++o) newpos[o] = nt++;
+    for (int o = c; o < b; ++o)
+        if (!((best_set >> (o - c)) & 1)) newpos[o] = nt++;
+    for (int o = c; o < b; ++o)
+        if ((best_set >> (o - c)) & 1) newpos[o] = nt++;
+    if (nt != b || (b - le) != tb) return false;
+    PassDesc q = pd;
+    for (int o = 0; o < b; ++o) q.tile_pos[newpos[o]] = pd.tile_pos[o];
+    // bonds with their new offset bits, grouped by thread mask (own group last)
+    int tmask[FTK_MAX_PASS_BONDS];
+    for (int l = 0; l < nb; ++l) {
+        const int bi = newpos[pd.bi[l]], bj = newpos[pd.bj[l]];
+        tmask[l] = ((1 << bi) | (1 << bj)) & ((1 << tb) - 1);
+    }
+    // stable order: distinct nonzero masks in first-appearance order, then 0
+    int gm[FTK_MAX_PASS_BONDS + 1], ng = 0;
+    for (int l = 0; l < nb; ++l) {
+        if (tmask[l] == 0) continue;
+        bool seen = false;
+        for (int g = 0; g < ng; ++g) seen |= gm[g] == tmask[l];
+        if (!seen) gm[ng++] = tmask[l];
+    }
+    gm[ng++] = 0;
+    int w = 0;
+    for (int g = 0; g < ng; ++g) {
+        for (int l = 0; l < nb; ++l) {
+            if (tmask[l] != gm[g]) continue;
+            const int bi = newpos[pd.bi[l]], bj = newpos[pd.bj[l]];
+            q.bi[w] = bi;
+            q.bj[w] = bj;
+            q.par[w] = pd.par[l];
+            q.anti[w] = pd.anti[l];
+            q.par_f[w] = pd.par_f[l];
+            q.anti_f[w] = pd.anti_f[l];
+            q.dgc[w] = pd.dgc[l];
+            const int km = ((1 << bi) | (1 << bj)) >> tb;
+            int ka = -1, kb = -1;
+            for (int a = 0; a < le; ++a)
+                if ((km >> a) & 1) { if (ka < 0) ka = a; else kb = a; }
+            q.bcase[w] = (int8_t)(ka < 0 ? 0 : kb < 0 ? 1 + ka : 5 + 4 * ka + kb);
+            ++w;
+        }
+        q.grp_tmask[g] = gm[g];
+        q.grp_end[g] = w;
+    }
+    if (w != nb) return false;
+    q.n_groups = ng;
+    q.le = le;
+    pd = q;
+    return true;
+}
+
+template <typename K>
+static cudaError_t opt_in(K kern) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
+template <typename R, int B, int LE>
+static cudaError_t attrs_le() {
+    cudaError_t e = opt_in(hv_pass_kernel<R, B, LE, EPI_PLAIN>);
+    if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, B, LE, EPI_COCG>);
+    if constexpr (B == 1)
+        if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, 1, LE, EPI_TPQ>);
+    return e;
+}
+
+template <typename R, int B, int LEDEF>
+static cudaError_t attrs_b() {
+    cudaError_t e = attrs_le<R, B, LEDEF>();
+    if (e == cudaSuccess && LEDEF != 0) e = attrs_le<R, B, 0>();
+    return e;
+}
+
+// Opt every H.V pass instantiation into the full shared memory once per
+// process (outside any stream capture).
+cudaError_t init_kernel_attributes() {
+    static int done = 0;
+    static cudaError_t status = cudaSuccess;
+    if (done) return status;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = attrs_b<double, 1, 3>();
+    if (e == cudaSuccess) e = attrs_b<double, 2, 2>();
+    if (e == cudaSuccess) e = attrs_b<double, 4, 1>();
+    if (e == cudaSuccess) e = attrs_b<double, 8, 0>();
+    if (e == cudaSuccess) e = attrs_b<float, 1, 4>();
+    if (e == cudaSuccess) e = attrs_b<float, 2, 3>();
+    if (e == cudaSuccess) e = attrs_b<float, 4, 2>();
+    if (e == cudaSuccess) e = attrs_b<float, 8, 1>();
+    status = e;
+    done = 1;
+    return e;
+}
+
+template <typename R, int B, int LE>
+static cudaError_t launch_le(int epi, const void *in, void *out, long long ld, const PassDesc &pd, const EpiArgs &ea,
+                             int grid_cap, cudaStream_t st) {
+    typedef typename C2<R>::t cx;
+    void (*k)(const cx *, cx *, long long, const PassDesc, const EpiArgs) = nullptr;
+    if (epi == EPI_PLAIN) k = hv_pass_kernel<R, B, LE, EPI_PLAIN>;
+    else if (epi == EPI_COCG) k = hv_pass_kernel<R, B, LE, EPI_COCG>;
+    else if constexpr (B == 1) {
+        if (epi == EPI_TPQ) k = hv_pass_kernel<R, 1, LE, EPI_TPQ>;
+    }
+    if (!k) return cudaErrorInvalidValue;
+    const int threads = hv_threads(pd);
+    const size_t smem = hv_smem_bytes(sizeof(R) == 8 ? 0 : 1, B, pd);
+    // persistent grid: the CTAs that are resident at once
+    int per_sm = 0, dev = 0, n_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long n_tiles = 1L << pd.n_free;
+    long g = (long)per_sm * n_sm;
+    if (g > n_tiles) g = n_tiles;
+    if (g > grid_cap) g = grid_cap;   // the caller's partial buffers
+    k<<<(int)g, threads, smem, st>>>(reinterpret_cast<const cx *>(in), reinterpret_cast<cx *>(out), ld, pd, ea);
+    return cudaGetLastError();
+}
+
+template <typename R, int B, int LEDEF>
+static cudaError_t launch_b(int epi, const void *in, void *out, long long ld, const PassDesc &pd, const EpiArgs &ea,
+                            int grid_cap, cudaStream_t st) {
+    if (pd.le == LEDEF) return launch_le<R, B, LEDEF>(epi, in, out, ld, pd, ea, grid_cap, st);
+    if (pd.le == 0) return launch_le<R, B, 0>(epi, in, out, ld, pd, ea, grid_cap, st);
+    return cudaErrorInvalidValue;
+}
+
+template <typename R>
+static cudaError_t launch_chunk(int bc, int epi, const void *in, void *out, long long ld, const PassDesc &pd,
+                                const EpiArgs &ea, int grid_cap, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        switch (bc) {
+        case 1: return launch_b<R, 1, 4>(epi, in, out, ld, pd, ea, grid_cap, st);
+        case 2: return launch_b<R, 2, 3>(epi, in, out, ld, pd, ea, grid_cap, st);
+        case 4: return launch_b<R, 4, 2>(epi, in, out, ld, pd, ea, grid_cap, st);
+        case 8: return launch_b<R, 8, 1>(epi, in, out, ld, pd, ea, grid_cap, st);
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (bc) {
+        case 1: return launch_b<R, 1, 3>(epi, in, out, ld, pd, ea, grid_cap, st);
+        case 2: return launch_b<R, 2, 2>(epi, in, out, ld, pd, ea, grid_cap, st);
+        case 4: return launch_b<R, 4, 1>(epi, in, out, ld, pd, ea, grid_cap, st);
+        case 8: return launch_b<R, 8, 0>(epi, in, out, ld, pd, ea, grid_cap, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+}
+
+cudaError_t launch_hv_pass(int prec, int B, int epi, const void *in, void *out, const PassDesc &pd,
+                           const EpiArgs &ea, int grid_cap, cudaStream_t st) {
+    if (B < 1 || (B & (B - 1)) || B > FTK_MAX_RHS || pd.le != hv_le(prec, B, pd.tile_bits, pd.chunk_bits) ||
+        hv_threads(pd) > 512 || (epi == EPI_TPQ && B != 1))
+        return cudaErrorInvalidConfiguration;
+    const int bc = std::min(B, hv_max_b(prec));
+    const size_t es = prec == 0 ? 16 : 8;
+    for (int j0 = 0; j0 < B; j0 += bc) {
+        EpiArgs e = ea;
+        if (e.result) e.result += 2 * j0;   // COCG: mu of columns j0 .. j0 + bc
+        const long long ld = 1LL << pd.n_sites;   // column stride: one vector
+        const void *i = static_cast<const char *>(in) + (size_t)j0 * ld * es;
+        void *o = static_cast<char *>(out) + (size_t)j0 * ld * es;
+        const cudaError_t r = prec == 0 ? launch_chunk<double>(bc, epi, i, o, ld, pd, e, grid_cap, st)
+                                        : launch_chunk<float>(bc, epi, i, o, ld, pd, e, grid_cap, st);
+        if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace ftk

@@ -1,8 +1,7 @@
 // CUDA kernels of the FTKomega hot path (sm_103a). No tensor cores: the
 // Hamiltonian-vector product is a bit-indexed gather, not a contraction.
 //
-//   hv_pass     one tiled pass of H.V (Sec. IV.A "Lanczos step"), fused
-//               epilogues for the mTPQ step (Appendix A) and the COCG mu dot
+//   (the H.V pass lives in ftk_hv.cu)
 //   cocg_update 3-term seed-COCG residual update with fused dots (Sec. II.B)
 //   cocg_seed   per-RHS seed scalars alpha_k, c_k and convergence test
 //   cocg_shift  per-shift recurrences pi, alpha^s, beta^s, projected p, G
@@ -14,329 +13,98 @@
 // the last CTA to finish (ticket from an integer atomic) sums the partials in
 // a fixed order and writes the result. No floating-point atomics.
 #include "ftk_common.cuh"
+#include "ftk_device.cuh"
 #include "ftk_kernels.h"
 
 #include <math.h>
 
 namespace ftk {
 
-// ---------------------------------------------------------------- complex
-template <typename R> struct C2;
-template <> struct C2<double> { typedef double2 t; };
-template <> struct C2<float> { typedef float2 t; };
-
-template <typename R>
-__device__ __forceinline__ typename C2<R>::t mk(R a, R b) {
-    typename C2<R>::t z; z.x = a; z.y = b; return z;
-}
-
-// ------------------------------------------------ per-thread dot accumulator
-// double: plain sum. float: the product of two floats is split exactly into
-// p + e with an FMA (two-product) and both parts enter a Knuth two-sum
-// compensated float accumulator, converted to double once per thread.
-template <typename R> struct Acc;
-template <> struct Acc<double> {
-    double s;
-    __device__ Acc() : s(0.0) {}
-    __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ void fma2(double a, double b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double get() const { return s; }
-};
-template <> struct Acc<float> {
-    float s, c;
-    __device__ Acc() : s(0.f), c(0.f) {}
-    __device__ __forceinline__ void add(float v) {
-        float t = s + v;
-        float bp = t - s;
-        float err = (s - (t - bp)) + (v - bp);
-        s = t;
-        c += err;
-    }
-    __device__ __forceinline__ void fma2(float a, float b) {
-        float p = a * b;
-        float e = fmaf(a, b, -p);
-        add(p);
-        c += e;
-    }
-    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
-};
-
-// ---------------------------------------------------------- reductions
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Reduce nd values per thread over the block (fixed order) into red[0..nd).
-// red must hold (blockDim/32) * nd doubles. Result valid in red[0..nd) after
-// the trailing __syncthreads.
-template <int ND>
-__device__ void block_reduce(double (&v)[ND], double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) v[d] = warp_sum(v[d]);
-    __syncthreads();
-    if (lane == 0) {
-#pragma unroll
-        for (int d = 0; d < ND; ++d) red[warp * ND + d] = v[d];
-    }
-    __syncthreads();
-    if (threadIdx.x < ND) {
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += red[w * ND + threadIdx.x];
-        red[threadIdx.x] = s;   // each thread reads column tid, writes slot tid
-    }
-    __syncthreads();
-}
-
-// Called by every thread of every CTA after it stored its ND partials at
-// partials[blockIdx.x * ND + d]. Returns true in the (unique) last CTA, after
-// it reduced all partials into out[0..ND) in a fixed order. Resets counter.
-template <int ND>
-__device__ bool last_block_reduce(const double *partials, unsigned int *counter, double *out,
-                                  double *red) {
-    __shared__ int am_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!am_last) return false;
-    __threadfence();
-    double v[ND];
-#pragma unroll
-    for (int d = 0; d < ND; ++d) v[d] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-#pragma unroll
-        for (int d = 0; d < ND; ++d) v[d] += __ldcg(partials + (size_t)b * ND + d);
-    }
-    block_reduce<ND>(v, red);
-    if (threadIdx.x < ND) out[threadIdx.x] = red[threadIdx.x];
-    if (threadIdx.x == 0) *counter = 0u;
-    __syncthreads();
-    return true;
-}
-
-// Bond coefficients in the kernel's arithmetic type (no per-element conversion).
-template <typename R> struct Coef;
-template <> struct Coef<double> {
-    __device__ static __forceinline__ double par(const PassDesc &p, int l) { return p.par[l]; }
-    __device__ static __forceinline__ double anti(const PassDesc &p, int l) { return p.anti[l]; }
-    __device__ static __forceinline__ double dgv(const PassDesc &p, int c) { return p.dgv[c]; }
-};
-template <> struct Coef<float> {
-    __device__ static __forceinline__ float par(const PassDesc &p, int l) { return p.par_f[l]; }
-    __device__ static __forceinline__ float anti(const PassDesc &p, int l) { return p.anti_f[l]; }
-    __device__ static __forceinline__ float dgv(const PassDesc &p, int c) { return p.dgv_f[c]; }
-};
-
-// ------------------------------------------------------------ H.V pass
-// Tile offset o (0 <= o < 2^b) -> global index base(t) + (o & chunk) | hi[o >> c].
-// Each thread owns offsets o = tid, tid + nthreads, ...; B right-hand sides
-// per amplitude are stored contiguously (layout [2^N][B]).
-template <typename R, int B, int EPI>
-__global__ void __launch_bounds__(B >= 8 ? 256 : 512)
-hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
-               const PassDesc pd, const EpiArgs ea) {
-    typedef typename C2<R>::t cx;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (ea.all_done && *ea.all_done) return;
-    const int b = pd.tile_bits, c = pd.chunk_bits;
-    const int tile_n = 1 << b;
-    const int n_hi = 1 << (b - c);
-    cx *tile = reinterpret_cast<cx *>(smem_raw);
-    uint32_t *hi = reinterpret_cast<uint32_t *>(smem_raw + (size_t)tile_n * B * sizeof(cx));
-    double *red = reinterpret_cast<double *>(hi + n_hi + (n_hi & 1));
-
-    for (int h = threadIdx.x; h < n_hi; h += blockDim.x) {
-        uint32_t off = 0;
-        for (int k = 0; k < b - c; ++k)
-            if ((h >> k) & 1) off |= 1u << pd.tile_pos[c + k];
-        hi[h] = off;
-    }
-    const R scale = (EPI == EPI_TPQ) ? (R)(*ea.scale) : (R)1;
-    const R ell = (R)ea.ell, inv_n = (R)ea.inv_n;
-    constexpr int ND = (EPI == EPI_TPQ) ? 2 : (EPI == EPI_COCG ? 2 * B : 1);
-    Acc<R> dot[ND];
-
-    const long n_tiles = 1L << pd.n_free;
-    const uint32_t cmask = (1u << c) - 1u;
-    for (long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        uint64_t base = 0;
-        for (int k = 0; k < pd.n_free; ++k)
-            if ((t >> k) & 1) base |= 1ull << pd.free_pos[k];
-        __syncthreads();   // hi[] ready / previous tile consumed
-        for (int idx = threadIdx.x; idx < tile_n * B; idx += blockDim.x) {
-            const int o = idx / B, j = idx % B;
-            const uint64_t x = base + ((o & cmask) | hi[o >> c]);
-            tile[idx] = in[x * B + j];
-        }
-        __syncthreads();
-        for (int o = threadIdx.x; o < tile_n; o += blockDim.x) {
-            const uint64_t x = base + ((o & cmask) | hi[o >> c]);
-            R ar[B], ai[B];
-            if (pd.first) {
-#pragma unroll
-                for (int j = 0; j < B; ++j) { ar[j] = 0; ai[j] = 0; }
-            } else {
-#pragma unroll
-                for (int j = 0; j < B; ++j) { cx p = out[x * B + j]; ar[j] = p.x; ai[j] = p.y; }
-            }
-            int c0 = 0, c1 = 0;
-            for (int l = 0; l < pd.n_bonds; ++l) {
-                const int bi = pd.bi[l], bj = pd.bj[l];
-                const int anti = ((o >> bi) ^ (o >> bj)) & 1;
-                const R coef = anti ? Coef<R>::anti(pd, l) : Coef<R>::par(pd, l);
-                const int sgn = 1 - 2 * anti;
-                if (pd.dgc[l]) c1 += sgn; else c0 += sgn;
-                const int po = o ^ (1 << bi) ^ (1 << bj);
-#pragma unroll
-                for (int j = 0; j < B; ++j) {
-                    cx p = tile[po * B + j];
-                    ar[j] = fma(coef, p.x, ar[j]);
-                    ai[j] = fma(coef, p.y, ai[j]);
-                }
-            }
-            const R dsum = Coef<R>::dgv(pd, 0) * (R)c0 + Coef<R>::dgv(pd, 1) * (R)c1;
-#pragma unroll
-            for (int j = 0; j < B; ++j) {
-                cx v = tile[o * B + j];
-                ar[j] = fma(dsum, v.x, ar[j]);
-                ai[j] = fma(dsum, v.y, ai[j]);
-            }
-            if (!pd.last || EPI == EPI_PLAIN) {
-#pragma unroll
-                for (int j = 0; j < B; ++j) out[x * B + j] = mk<R>(ar[j], ai[j]);
-            } else if (EPI == EPI_TPQ) {
-                // psi' = s (l v - H v / N);  <v|Hv>, |psi'|^2
-                cx v = tile[o];
-                R yr = scale * (ell * v.x - inv_n * ar[0]);
-                R yi = scale * (ell * v.y - inv_n * ai[0]);
-                out[x] = mk<R>(yr, yi);
-                dot[0].fma2(v.x, ar[0]);
-                dot[0].fma2(v.y, ai[0]);
-                dot[1].fma2(yr, yr);
-                dot[1].fma2(yi, yi);
-            } else {
-                // W = H R;  mu_j = R_j^T W_j (bilinear)
-#pragma unroll
-                for (int j = 0; j < B; ++j) {
-                    cx v = tile[o * B + j];
-                    out[x * B + j] = mk<R>(ar[j], ai[j]);
-                    dot[2 * j].fma2(v.x, ar[j]);
-                    dot[2 * j].fma2(-v.y, ai[j]);
-                    dot[2 * j + 1].fma2(v.x, ai[j]);
-                    dot[2 * j + 1].fma2(v.y, ar[j]);
-                }
-            }
-        }
-    }
-    if (EPI == EPI_PLAIN || !pd.last) return;
-
-    double v[ND];
-#pragma unroll
-    for (int d = 0; d < ND; ++d) v[d] = dot[d].get();
-    block_reduce<ND>(v, red);
-    if (threadIdx.x < ND) ea.partials[(size_t)blockIdx.x * ND + threadIdx.x] = red[threadIdx.x];
-    double *res = ea.result;
-    if (!last_block_reduce<ND>(ea.partials, ea.counter, res, red)) return;
-    if (EPI == EPI_TPQ && threadIdx.x == 0) {
-        // mTPQ statistics of step k (Appendix A): u_k = s^2 <v|Hv>/N,
-        // q_k = ||psi'||, <H^2>_k = N^2 (q^2 - l^2 + 2 l u_k)
-        TpqState *st = ea.tpq;
-        const double s = st->scale, n = st->n_sites, l = st->ell;
-        const double u = s * s * res[0] / n;
-        const double q2 = res[1];
-        const int k = st->k;
-        ea.stat_u[k] = u;
-        ea.stat_logq[k] = st->logQ;
-        ea.stat_h2[k] = n * n * (q2 - l * l + 2.0 * l * u);
-        st->logQ += 0.5 * log(q2);
-        st->scale = 1.0 / sqrt(q2);
-        st->k = k + 1;
-    }
-}
-
 // --------------------------------------------------------- COCG update
-// mode 0: R_new = lambda_j (start);  mode 1: 3-term seed residual update
+// Block vectors are stored RHS by RHS: element (x, j) at j * dim + x.
+// Grid (gx, B): blockIdx.y = j.
+// mode 0: r_0 = lambda_j (start);  mode 1: 3-term seed residual update
 //   r_{k+1} = (1 + c_k) r_k - alpha_k (z_s r_k - w_k) - c_k r_{k-1}
-// written over r_{k-1}. Fused dots of r_{k+1}: rho = r^T r, g = lambda^dag r,
-// |r|^2 (per RHS, FTK_UPD_DOTS doubles each).
-template <typename R, int B>
+// evaluated as r_k + c_k (r_k - r_{k-1}) - alpha_k (z_s r_k - w_k) and written
+// over r_{k-1}. z_s r - w is formed by FMAs from a hi + lo split of z_s
+// (exact products, one rounding of the small difference), so FP32 vectors
+// lose no digits to the cancellation between z_s r and H r. Fused dots of
+// r_{k+1}: rho = r^T r, g = lambda^dag r, |r|^2 (FTK_UPD_DOTS doubles per RHS).
+// A finished RHS (done != 0) is skipped; its block contributes zeros.
+template <typename R>
 __global__ void __launch_bounds__(256)
 cocg_update_kernel(const typename C2<R>::t *__restrict__ rcur, const typename C2<R>::t *__restrict__ w,
                    typename C2<R>::t *rprev_new, UpdArgs ua) {
     typedef typename C2<R>::t cx;
-    __shared__ double red[(256 / 32) * FTK_UPD_DOTS * B];
+    __shared__ double red[(256 / 32) * 5];
     if (*ua.all_done) return;
-    const uint64_t total = ua.dim * B;
-    const int j = threadIdx.x % B;     // blockDim and stride are multiples of B
-    R a_re = 1, a_im = 0, b_re = 0, b_im = 0, c_re = 0, c_im = 0;
+    const int j = blockIdx.y;
+    const uint64_t n = ua.dim;
+    const size_t off = (size_t)j * n;
+    const bool skip = ua.mode == 1 && ua.seed[j].done != 0;
+    R zr_hi = 0, zr_lo = 0, zi_hi = 0, zi_lo = 0, al_re = 0, al_im = 0, c_re = 0, c_im = 0;
     if (ua.mode == 1) {
         const CocgSeed &s = ua.seed[j];
-        // a = 1 + c - alpha z_s, b = alpha, c' = -c
-        a_re = (R)(1.0 + s.c_re - (s.alpha_re * s.zs_re - s.alpha_im * s.zs_im));
-        a_im = (R)(s.c_im - (s.alpha_re * s.zs_im + s.alpha_im * s.zs_re));
-        b_re = (R)s.alpha_re; b_im = (R)s.alpha_im;
-        c_re = (R)(-s.c_re); c_im = (R)(-s.c_im);
+        zr_hi = (R)s.zs_re; zr_lo = (R)(s.zs_re - (double)zr_hi);
+        zi_hi = (R)s.zs_im; zi_lo = (R)(s.zs_im - (double)zi_hi);
+        al_re = (R)s.alpha_re; al_im = (R)s.alpha_im;
+        c_re = (R)s.c_re; c_im = (R)s.c_im;
     }
     const cx *lam = reinterpret_cast<const cx *>(ua.lambda[j]);
     Acc<R> d_rr, d_ri, d_gr, d_gi, d_n;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t x = i / B;
-        const cx l = lam[x];
-        cx r;
-        if (ua.mode == 0) {
-            r = l;
-        } else {
-            const cx rc = rcur[i], wc = w[i], rp = rprev_new[i];
-            R re = a_re * rc.x - a_im * rc.y;
-            R im = a_re * rc.y + a_im * rc.x;
-            re = fma(b_re, wc.x, re); re = fma(-b_im, wc.y, re);
-            im = fma(b_re, wc.y, im); im = fma(b_im, wc.x, im);
-            re = fma(c_re, rp.x, re); re = fma(-c_im, rp.y, re);
-            im = fma(c_re, rp.y, im); im = fma(c_im, rp.x, im);
-            r = mk<R>(re, im);
+    if (!skip) {
+        for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+             x += (uint64_t)gridDim.x * blockDim.x) {
+            const cx l = lam[x];
+            cx r;
+            if (ua.mode == 0) {
+                r = l;
+            } else {
+                const cx rc = rcur[off + x], wc = w[off + x], rp = rprev_new[off + x];
+                // A r = z_s r - w
+                R ar = fma(zr_hi, rc.x, -wc.x);
+                ar = fma(-zi_hi, rc.y, ar);
+                ar = fma(zr_lo, rc.x, ar);
+                ar = fma(-zi_lo, rc.y, ar);
+                R ai = fma(zr_hi, rc.y, -wc.y);
+                ai = fma(zi_hi, rc.x, ai);
+                ai = fma(zr_lo, rc.y, ai);
+                ai = fma(zi_lo, rc.x, ai);
+                // d = c (r - r_prev) - alpha A r
+                const R tr = rc.x - rp.x, ti = rc.y - rp.y;
+                R dr = c_re * tr - c_im * ti;
+                R di = c_re * ti + c_im * tr;
+                dr = fma(-al_re, ar, dr); dr = fma(al_im, ai, dr);
+                di = fma(-al_re, ai, di); di = fma(-al_im, ar, di);
+                r = mk<R>(rc.x + dr, rc.y + di);
+            }
+            rprev_new[off + x] = r;
+            d_rr.fma2(r.x, r.x); d_rr.fma2(-r.y, r.y);
+            d_ri.fma2(2 * r.x, r.y);
+            d_gr.fma2(l.x, r.x); d_gr.fma2(l.y, r.y);
+            d_gi.fma2(l.x, r.y); d_gi.fma2(-l.y, r.x);
+            d_n.fma2(r.x, r.x); d_n.fma2(r.y, r.y);
         }
-        rprev_new[i] = r;
-        d_rr.fma2(r.x, r.x); d_rr.fma2(-r.y, r.y);
-        d_ri.fma2(2 * r.x, r.y);
-        d_gr.fma2(l.x, r.x); d_gr.fma2(l.y, r.y);
-        d_gi.fma2(l.x, r.y); d_gi.fma2(-l.y, r.x);
-        d_n.fma2(r.x, r.x); d_n.fma2(r.y, r.y);
     }
-    // reduce lanes that share j (xor offsets >= B keep j fixed)
     double v[5] = {d_rr.get(), d_ri.get(), d_gr.get(), d_gi.get(), d_n.get()};
-#pragma unroll
-    for (int d = 0; d < 5; ++d)
-        for (int o = 16; o >= B; o >>= 1) v[d] += __shfl_xor_sync(0xffffffffu, v[d], o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane < B) {
-#pragma unroll
-        for (int d = 0; d < 5; ++d) red[(warp * B + lane) * FTK_UPD_DOTS + d] = v[d];
-    }
-    __syncthreads();
-    double *part = ua.partials + (size_t)blockIdx.x * B * FTK_UPD_DOTS;
-    for (int q = threadIdx.x; q < B * FTK_UPD_DOTS; q += blockDim.x) {
-        double s = 0.0;
-        if (q % FTK_UPD_DOTS < 5)
-            for (int ww = 0; ww < nw; ++ww) s += red[ww * B * FTK_UPD_DOTS + q];
-        part[q] = s;
-    }
-    // last block: fixed-order sum of all partials -> ua.result[B][FTK_UPD_DOTS]
+    block_reduce<5>(v, red);
+    const unsigned nblk = gridDim.x * gridDim.y;
+    double *part = ua.partials + ((size_t)j * gridDim.x + blockIdx.x) * 5;
+    if (threadIdx.x < 5) part[threadIdx.x] = red[threadIdx.x];
+    // last block: fixed-order sum of the partials -> ua.result[B][FTK_UPD_DOTS]
     __shared__ int am_last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) am_last = (atomicAdd(ua.counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) am_last = (atomicAdd(ua.counter, 1u) == nblk - 1);
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    for (int q = threadIdx.x; q < B * FTK_UPD_DOTS; q += blockDim.x) {
-        double s = 0.0;
-        for (int bb = 0; bb < (int)gridDim.x; ++bb)
-            s += __ldcg(ua.partials + (size_t)bb * B * FTK_UPD_DOTS + q);
-        ua.result[q] = s;
+    for (int q = threadIdx.x; q < (int)gridDim.y * 5; q += blockDim.x) {
+        const int jj = q / 5, d = q % 5;
+        double sum = 0.0;
+        for (unsigned bb = 0; bb < gridDim.x; ++bb)
+            sum += __ldcg(ua.partials + ((size_t)jj * gridDim.x + bb) * 5 + d);
+        ua.result[jj * FTK_UPD_DOTS + d] = sum;
     }
     if (threadIdx.x == 0) *ua.counter = 0u;
 }
@@ -704,115 +472,19 @@ __global__ void __launch_bounds__(256) spectrum_kernel(SpecArgs sp) {
 }
 
 // ================================================================ launchers
-template <typename R, int B>
-static cudaError_t hv_dispatch_epi(int epi, const void *in, void *out, const PassDesc &pd,
-                                   const EpiArgs &ea, int grid, int threads, size_t smem,
-                                   cudaStream_t st) {
-    typedef typename C2<R>::t cx;
-    void (*k)(const cx *, cx *, const PassDesc, const EpiArgs) = nullptr;
-    if (epi == EPI_PLAIN) k = hv_pass_kernel<R, B, EPI_PLAIN>;
-    else if (epi == EPI_COCG) k = hv_pass_kernel<R, B, EPI_COCG>;
-    else if (epi == EPI_TPQ) {
-        if (B != 1) return cudaErrorInvalidValue;
-        k = hv_pass_kernel<R, 1, EPI_TPQ>;
-    }
-    if (!k) return cudaErrorInvalidValue;
-    k<<<grid, threads, smem, st>>>(reinterpret_cast<const cx *>(in), reinterpret_cast<cx *>(out), pd, ea);
-    return cudaGetLastError();
-}
-
-template <typename R>
-static cudaError_t hv_dispatch_b(int B, int epi, const void *in, void *out, const PassDesc &pd,
-                                 const EpiArgs &ea, int grid, int threads, size_t smem, cudaStream_t st) {
-    switch (B) {
-    case 1: return hv_dispatch_epi<R, 1>(epi, in, out, pd, ea, grid, threads, smem, st);
-    case 2: return hv_dispatch_epi<R, 2>(epi, in, out, pd, ea, grid, threads, smem, st);
-    case 4: return hv_dispatch_epi<R, 4>(epi, in, out, pd, ea, grid, threads, smem, st);
-    case 8: return hv_dispatch_epi<R, 8>(epi, in, out, pd, ea, grid, threads, smem, st);
-    case 16: return hv_dispatch_epi<R, 16>(epi, in, out, pd, ea, grid, threads, smem, st);
-    case 32: return hv_dispatch_epi<R, 32>(epi, in, out, pd, ea, grid, threads, smem, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-// Opt every H.V pass instantiation into the full 227 KB of shared memory
-// once per process (must happen outside stream capture).
-template <typename K>
-static cudaError_t opt_in(K kern) {
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-    return e;
-}
-
-template <typename R, int B>
-static cudaError_t attrs_b() {
-    cudaError_t e = opt_in(hv_pass_kernel<R, B, EPI_PLAIN>);
-    if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, B, EPI_COCG>);
-    if (e == cudaSuccess && B == 1) e = opt_in(hv_pass_kernel<R, 1, EPI_TPQ>);
-    return e;
-}
-
-cudaError_t init_kernel_attributes() {
-    static int done = 0;
-    static cudaError_t status = cudaSuccess;
-    if (done) return status;
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = attrs_b<double, 1>();
-    if (e == cudaSuccess) e = attrs_b<double, 2>();
-    if (e == cudaSuccess) e = attrs_b<double, 4>();
-    if (e == cudaSuccess) e = attrs_b<double, 8>();
-    if (e == cudaSuccess) e = attrs_b<double, 16>();
-    if (e == cudaSuccess) e = attrs_b<double, 32>();
-    if (e == cudaSuccess) e = attrs_b<float, 1>();
-    if (e == cudaSuccess) e = attrs_b<float, 2>();
-    if (e == cudaSuccess) e = attrs_b<float, 4>();
-    if (e == cudaSuccess) e = attrs_b<float, 8>();
-    if (e == cudaSuccess) e = attrs_b<float, 16>();
-    if (e == cudaSuccess) e = attrs_b<float, 32>();
-    status = e;
-    done = 1;
-    return e;
-}
-
-cudaError_t launch_hv_pass(int prec, int B, int epi, const void *in, void *out, const PassDesc &pd,
-                           const EpiArgs &ea, int grid, int threads, size_t smem, cudaStream_t st) {
-    if (prec == 0) return hv_dispatch_b<double>(B, epi, in, out, pd, ea, grid, threads, smem, st);
-    return hv_dispatch_b<float>(B, epi, in, out, pd, ea, grid, threads, smem, st);
-}
-
-size_t hv_smem_bytes(int prec, int B, int tile_bits, int chunk_bits, int threads) {
-    const size_t elem = prec == 0 ? 16 : 8;
-    const size_t n_hi = (size_t)1 << (tile_bits - chunk_bits);
-    const int nd = 2 * B > 2 ? 2 * B : 2;
-    return ((size_t)1 << tile_bits) * B * elem + (n_hi + (n_hi & 1)) * 4 + (size_t)(threads / 32) * nd * 8;
-}
-
-template <typename R>
-static cudaError_t upd_dispatch(int B, const void *rcur, const void *w, void *rprev_new,
-                                const UpdArgs &ua, int grid, cudaStream_t st) {
-    typedef typename C2<R>::t cx;
-#define FTK_UPD_CASE(BB)                                                                     \
-    case BB:                                                                                 \
-        cocg_update_kernel<R, BB><<<grid, 256, 0, st>>>(reinterpret_cast<const cx *>(rcur), \
-            reinterpret_cast<const cx *>(w), reinterpret_cast<cx *>(rprev_new), ua);         \
-        break;
-    switch (B) {
-        FTK_UPD_CASE(1) FTK_UPD_CASE(2) FTK_UPD_CASE(4) FTK_UPD_CASE(8) FTK_UPD_CASE(16) FTK_UPD_CASE(32)
-    default: return cudaErrorInvalidValue;
-    }
-#undef FTK_UPD_CASE
-    return cudaGetLastError();
-}
-
 cudaError_t launch_cocg_update(int prec, int B, const void *rcur, const void *w, void *rprev_new,
                                const UpdArgs &ua, int grid, cudaStream_t st) {
-    if (prec == 0) return upd_dispatch<double>(B, rcur, w, rprev_new, ua, grid, st);
-    return upd_dispatch<float>(B, rcur, w, rprev_new, ua, grid, st);
+    if (B < 1 || B > FTK_MAX_RHS) return cudaErrorInvalidValue;
+    const dim3 g(grid, B);
+    if (prec == 0)
+        cocg_update_kernel<double><<<g, 256, 0, st>>>(reinterpret_cast<const double2 *>(rcur),
+                                                      reinterpret_cast<const double2 *>(w),
+                                                      reinterpret_cast<double2 *>(rprev_new), ua);
+    else
+        cocg_update_kernel<float><<<g, 256, 0, st>>>(reinterpret_cast<const float2 *>(rcur),
+                                                     reinterpret_cast<const float2 *>(w),
+                                                     reinterpret_cast<float2 *>(rprev_new), ua);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cocg_seed(const SeedArgs &sa, cudaStream_t st) {

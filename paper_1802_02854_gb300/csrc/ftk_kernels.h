@@ -93,9 +93,18 @@ struct SpecArgs {
 
 cudaError_t init_kernel_attributes();
 void set_thread_error(const char *msg);   // message for ftk_last_error(NULL)
+// H.V pass (ftk_hv.cu). A planned pass is laid out once for the kernel's
+// thread layout (hv_layout_pass) before it is launched; B > hv_max_b(prec)
+// right-hand sides run as column chunks of hv_max_b(prec). grid_cap bounds
+// the persistent grid (the size of ea.partials).
 cudaError_t launch_hv_pass(int prec, int B, int epi, const void *in, void *out, const PassDesc &pd,
-                           const EpiArgs &ea, int grid, int threads, size_t smem, cudaStream_t st);
-size_t hv_smem_bytes(int prec, int B, int tile_bits, int chunk_bits, int threads);
+                           const EpiArgs &ea, int grid_cap, cudaStream_t st);
+bool hv_layout_pass(PassDesc &pd, int prec, int B);
+int hv_max_b(int prec);
+int hv_le(int prec, int B, int tile_bits, int chunk_bits);
+int hv_max_tile_bits(int prec, int B);
+int hv_threads(const PassDesc &pd);
+size_t hv_smem_bytes(int prec, int B, const PassDesc &pd);
 cudaError_t launch_cocg_update(int prec, int B, const void *rcur, const void *w, void *rprev_new,
                                const UpdArgs &ua, int grid, cudaStream_t st);
 cudaError_t launch_cocg_seed(const SeedArgs &sa, cudaStream_t st);

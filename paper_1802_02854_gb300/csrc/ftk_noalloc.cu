@@ -86,22 +86,16 @@ extern "C" ftk_status ftk_tpq_step_noalloc(int32_t n_sites, const ftk_bond *bond
     }
     NoallocScratch *s = g_scratch_ptr[dev];
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    int n_sm = 0;
-    e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return noalloc_fail(FTK_ECUDA, cudaGetErrorString(e));
 
-    // plan (stack only): FP64, one vector, 2^12-amplitude tiles
+    // plan (stack only): FP64, one vector
     PassDesc pd[FTK_MAX_PASSES];
     int tb = 0, cb = 0;
-    const int np = plan_hv_passes(n_sites, pb, n_bonds, K, J, 16, 1, 12, pd, FTK_MAX_PASSES, &tb, &cb);
+    const int np = plan_hv_passes(n_sites, pb, n_bonds, K, J, 16, 1, hv_max_tile_bits(0, 1), pd, FTK_MAX_PASSES,
+                                  &tb, &cb);
     if (np == 0) return noalloc_fail(FTK_EINVAL, "ftk_tpq_step_noalloc: pass planning failed");
-    const int threads = tb >= 9 ? 512 : (1 << tb);
-    const size_t smem = hv_smem_bytes(0, 1, tb, cb, threads);
-    const long n_tiles = 1L << (n_sites - tb);
-    const int per_sm = (int)((size_t(228) << 10) / (smem + 1024));
-    long grid = (long)(per_sm > 0 ? per_sm : 1) * n_sm;
-    if (grid > n_tiles) grid = n_tiles;
-    if (grid > kNoallocMaxGrid) grid = kNoallocMaxGrid;
+    for (int p = 0; p < np; ++p)
+        if (!hv_layout_pass(pd[p], 0, 1)) return noalloc_fail(FTK_EINVAL, "ftk_tpq_step_noalloc: pass layout failed");
+    const long grid = kNoallocMaxGrid;   // the launcher trims it to the resident CTAs
 
     // state of this step: normalised input (scale 1), log Q and k start at 0;
     // the ticket must start at zero
@@ -125,8 +119,7 @@ extern "C" ftk_status ftk_tpq_step_noalloc(int32_t n_sites, const ftk_bond *bond
     ea.stat_logq = &s->stats[1];
     ea.stat_h2 = &s->stats[2];
     for (int p = 0; p < np; ++p) {
-        e = launch_hv_pass(0, 1, p == np - 1 ? EPI_TPQ : EPI_PLAIN, psi_dev, out_dev, pd[p], ea, (int)grid,
-                           threads, smem, st);
+        e = launch_hv_pass(0, 1, p == np - 1 ? EPI_TPQ : EPI_PLAIN, psi_dev, out_dev, pd[p], ea, (int)grid, st);
         if (e != cudaSuccess) return noalloc_fail(FTK_ECUDA, cudaGetErrorString(e));
     }
     // q_k = 1 / (new scale); copy u_k, <H^2>_k and q_k back
