@@ -20,7 +20,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libftk.so")
 
 FTK_OK, FTK_EINVAL, FTK_ENOMEM, FTK_ECUDA, FTK_ENOCONV, FTK_EBREAKDOWN, FTK_ETIMEOUT, FTK_ETRUNC, FTK_EBUSY = range(9)
-FTK_FP64, FTK_FP32 = 0, 1
+FTK_FP64, FTK_FP32, FTK_MIXED = 0, 1, 2
+PRECISIONS = {"fp64": FTK_FP64, "fp32": FTK_FP32, "mixed": FTK_MIXED}
 STATUS_NAMES = ["FTK_OK", "FTK_EINVAL", "FTK_ENOMEM", "FTK_ECUDA", "FTK_ENOCONV", "FTK_EBREAKDOWN",
                 "FTK_ETIMEOUT", "FTK_ETRUNC", "FTK_EBUSY"]
 
@@ -254,7 +255,8 @@ class Context:
     """A context plus the torch device workspace it runs in.
 
     cluster: object with n_sites, pos [N, 2], bonds [n_bonds, 3].
-    precision: "fp64" or "fp32". stream: torch.cuda.Stream (default: a new one).
+    precision: "fp64", "fp32" or "mixed" (FP32 H.v, FP64 Krylov vectors).
+    stream: torch.cuda.Stream (default: a new one).
     """
 
     def __init__(self, cluster, K, J, precision="fp64", max_rhs=1, n_saved=1, tile_bits=0, stream=None,
@@ -264,7 +266,7 @@ class Context:
         self.torch = torch
         self.n = int(cluster.n_sites)
         self.dim = 1 << self.n
-        self.prec = FTK_FP64 if precision in ("fp64", FTK_FP64) else FTK_FP32
+        self.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.max_rhs = max_rhs
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.handle = ftk_create(self.n, cluster.pos, cluster.bonds, K, J, self.prec, max_rhs, n_saved,

@@ -34,12 +34,12 @@ const int kShiftArrays = 5;
 
 Layout make_layout(int n, int n_saved, int max_rhs, int prec) {
     Layout L{};
-    const size_t es = prec == FTK_FP64 ? 16 : 8;
+    const size_t es = prec == FTK_FP32 ? 8 : 16;   // FTK_MIXED stores FP64 vectors
     const size_t vb = (size_t(1) << n) * es;
     size_t off = 0;
     L.vec_bytes = vb;
     // the mTPQ state is always FP64 (16 B / amplitude); shells, probes and
-    // Krylov vectors use the context precision
+    // Krylov vectors use the context's vector precision
     const size_t vb64 = (size_t(1) << n) * 16;
     for (int i = 0; i < 2; ++i) { L.psi[i] = off; off = align_up(off + vb64); }
     L.shells = off; off = align_up(off + vb * n_saved);
@@ -81,6 +81,7 @@ void set_thread_error(const char *msg);
 
 struct ftk_ctx {
     int n = 0, nb = 0, prec = 0, max_rhs = 1, n_saved_cap = 1, tile_bits_req = 0;
+    int vprec = 0, mprec = 0;   // vector storage / H.v arithmetic: 0 FP64, 1 FP32
     uint64_t dim = 0;
     double K = 0, J = 0, ell_min = 0;
     std::vector<Bond> bonds;
@@ -236,7 +237,7 @@ extern "C" {
 
 size_t ftk_footprint(int32_t n_sites, int32_t n_saved, int32_t max_rhs, int32_t precision) {
     if (n_sites < 2 || n_sites > FTK_MAX_SITES || n_saved < 1 || max_rhs < 1 ||
-        max_rhs > FTK_MAX_RHS || (precision != FTK_FP64 && precision != FTK_FP32))
+        max_rhs > FTK_MAX_RHS || (precision != FTK_FP64 && precision != FTK_FP32 && precision != FTK_MIXED))
         return 0;
     return make_layout(n_sites, n_saved, max_rhs, precision).total;
 }
@@ -249,8 +250,8 @@ ftk_status ftk_create(const ftk_lattice *lat, const ftk_bond *bonds, int32_t n_b
     const int n = lat->n_sites;
     if (n < 2 || n > FTK_MAX_SITES) return fail(nullptr, FTK_EINVAL, "n_sites must be in [2, 30]");
     if (n_bonds < 1 || n_bonds > 2 * FTK_MAX_PASS_BONDS) return fail(nullptr, FTK_EINVAL, "bad n_bonds");
-    if (opts->precision != FTK_FP64 && opts->precision != FTK_FP32)
-        return fail(nullptr, FTK_EINVAL, "precision must be FTK_FP64 or FTK_FP32");
+    if (opts->precision != FTK_FP64 && opts->precision != FTK_FP32 && opts->precision != FTK_MIXED)
+        return fail(nullptr, FTK_EINVAL, "precision must be FTK_FP64, FTK_FP32 or FTK_MIXED");
     if (opts->max_rhs < 1 || opts->max_rhs > FTK_MAX_RHS || opts->n_saved < 1)
         return fail(nullptr, FTK_EINVAL, "max_rhs must be in [1, 32] and n_saved >= 1");
     if (!std::isfinite(K) || !std::isfinite(J)) return fail(nullptr, FTK_EINVAL, "K, J must be finite");
@@ -267,6 +268,8 @@ ftk_status ftk_create(const ftk_lattice *lat, const ftk_bond *bonds, int32_t n_b
     ctx->K = K;
     ctx->J = J;
     ctx->prec = opts->precision;
+    ctx->vprec = ctx->prec == FTK_FP32 ? 1 : 0;
+    ctx->mprec = ctx->prec == FTK_FP64 ? 0 : 1;
     ctx->max_rhs = opts->max_rhs;
     ctx->n_saved_cap = opts->n_saved;
     ctx->tile_bits_req = opts->tile_bits;
@@ -298,7 +301,7 @@ ftk_status ftk_create(const ftk_lattice *lat, const ftk_bond *bonds, int32_t n_b
         return fail(nullptr, FTK_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
     }
     Plan *pl = nullptr;
-    if (get_plan(ctx, ctx->prec, 1, &pl) != FTK_OK) {
+    if (get_plan(ctx, ctx->mprec, 1, &pl) != FTK_OK) {
         std::string m = ctx->err;
         ftk_destroy(ctx);
         return fail(nullptr, FTK_EINVAL, m);
@@ -423,10 +426,10 @@ ftk_status ftk_tpq_step(ftk_ctx *ctx, int32_t n_steps, int32_t save_every, doubl
         if (k % save_every == 0) {
             const int sidx = ctx->n_saved;
             void *dst = wsp(ctx, ctx->L.shells + ctx->L.vec_bytes * sidx);
-            if (ctx->prec == FTK_FP64)
+            if (ctx->vprec == 0)
                 CK(cudaMemcpyAsync(dst, cur, ctx->L.vec_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
             else
-                LAUNCH(launch_convert_in(ctx->prec, cur, dst, ctx->dim, vec_grid(ctx, ctx->dim), ctx->stream));
+                LAUNCH(launch_convert_in(ctx->vprec, cur, dst, ctx->dim, vec_grid(ctx, ctx->dim), ctx->stream));
             CK(cudaMemcpyAsync(ctx->shell_scale + sidx, &ctx->dsmall->tpq.scale, sizeof(double),
                                cudaMemcpyDeviceToDevice, ctx->stream));
             ctx->shell_step.resize(sidx + 1);
@@ -487,7 +490,7 @@ ftk_status ftk_apply_op(ftk_ctx *ctx, int32_t shell, int32_t gamma, const double
     oa.n_sites_d = ctx->n;
     oa.slot_energy = ctx->slot_energy + slot;
     oa.slot_norm2 = ctx->slot_norm2 + slot;
-    LAUNCH(launch_apply_op(ctx->prec, wsp(ctx, ctx->L.shells + ctx->L.vec_bytes * shell),
+    LAUNCH(launch_apply_op(ctx->vprec, wsp(ctx, ctx->L.shells + ctx->L.vec_bytes * shell),
                            wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * slot), oa, vec_grid(ctx, ctx->dim),
                            ctx->stream));
     ctx->slot_valid[slot] = 1;
@@ -498,7 +501,7 @@ ftk_status ftk_set_probe(ftk_ctx *ctx, int32_t slot, const double *v, int32_t is
     ftk_status s = check_ready(ctx);
     if (s) return s;
     if (slot < 0 || slot >= ctx->max_rhs || !v) return fail(ctx, FTK_EINVAL, "bad slot or vector");
-    if ((s = load_vector(ctx, v, is_device, wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * slot), ctx->prec))) return s;
+    if ((s = load_vector(ctx, v, is_device, wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * slot), ctx->vprec))) return s;
     CK(cudaMemcpyAsync(ctx->slot_energy + slot, &energy, sizeof energy, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->slot_valid[slot] = 1;
@@ -507,15 +510,21 @@ ftk_status ftk_set_probe(ftk_ctx *ctx, int32_t slot, const double *v, int32_t is
 
 // One blocked COCG iteration on the context stream (no host sync):
 // H R_cur -> W (+mu), seed scalars, shift recurrences, R_prev <- update.
+// Kind of the update kernel: 0 FP64 vectors, 1 FP32 vectors, 2 mixed (split
+// float hi + lo residuals; hi at the buffer start, lo ua.lo_stride float2
+// elements later).
+static int upd_kind(const ftk_ctx *ctx) { return ctx->prec == FTK_MIXED ? 2 : ctx->vprec; }
+
 static ftk_status cocg_iteration(ftk_ctx *ctx, int B, void *rcur, void *rprev, void *w,
-                                 const EpiArgs &ea, const SeedArgs &sa, const ShiftArgs &sh,
+                                 EpiArgs ea, const SeedArgs &sa, const ShiftArgs &sh,
                                  UpdArgs ua) {
-    ftk_status s = run_hv(ctx, ctx->prec, B, EPI_COCG, rcur, w, ea);
+    if (ctx->prec == FTK_MIXED) ea.lo = static_cast<const char *>(rcur) + size_t(8) * ua.lo_stride;
+    ftk_status s = run_hv(ctx, ctx->mprec, B, EPI_COCG, rcur, w, ea);
     if (s) return s;
     LAUNCH(launch_cocg_seed(sa, ctx->stream));
     LAUNCH(launch_cocg_shift(sh, B, ctx->stream));
     ua.mode = 1;
-    LAUNCH(launch_cocg_update(ctx->prec, B, rcur, w, rprev, ua, vec_grid(ctx, ctx->dim), ctx->stream));
+    LAUNCH(launch_cocg_update(upd_kind(ctx), B, rcur, w, rprev, ua, vec_grid(ctx, ctx->dim), ctx->stream));
     return FTK_OK;
 }
 
@@ -543,7 +552,7 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
         return s1 != FTK_OK ? s1 : s2;
     }
     Plan *pl = nullptr;
-    if ((s = get_plan(ctx, ctx->prec, B, &pl))) return s;
+    if ((s = get_plan(ctx, ctx->mprec, B, &pl))) return s;
     Small *d = ctx->dsmall;
     // per-RHS seed scalars: z_s = E_j + omega[mid] + i eta
     std::vector<double> e(n_rhs);
@@ -591,6 +600,7 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     ua.counter = &d->counters[3];
     ua.result = d->upd_dots;
     ua.all_done = &d->all_done;
+    ua.lo_stride = (long long)ctx->max_rhs * (long long)ctx->dim;   // mixed mode only
     EpiArgs ea{};
     ea.partials = (double *)wsp(ctx, ctx->L.partials);
     ea.counter = &d->counters[4];
@@ -616,9 +626,14 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     sh.tol = tol;
 
     // r_0 = lambda (+ dots); r_{-1} = 0 so that c_0 r_{-1} is exactly zero
-    CK(cudaMemsetAsync(rprev, 0, ctx->L.vec_bytes * B, ctx->stream));
+    if (ctx->prec == FTK_MIXED) {   // hi and lo parts of the B columns
+        CK(cudaMemsetAsync(rprev, 0, ctx->dim * 8 * B, ctx->stream));
+        CK(cudaMemsetAsync(static_cast<char *>(rprev) + size_t(8) * ua.lo_stride, 0, ctx->dim * 8 * B, ctx->stream));
+    } else {
+        CK(cudaMemsetAsync(rprev, 0, ctx->L.vec_bytes * B, ctx->stream));
+    }
     ua.mode = 0;
-    LAUNCH(launch_cocg_update(ctx->prec, B, nullptr, nullptr, rcur, ua, vec_grid(ctx, ctx->dim), ctx->stream));
+    LAUNCH(launch_cocg_update(upd_kind(ctx), B, nullptr, nullptr, rcur, ua, vec_grid(ctx, ctx->dim), ctx->stream));
 
     // Capture two iterations (buffer roles return to the start) in a graph.
     cudaGraph_t graph = nullptr;
@@ -721,7 +736,7 @@ ftk_status ftk_hv(ftk_ctx *ctx, const void *v_dev, void *out_dev, int32_t n_rhs)
     if (n_rhs < 1 || n_rhs > FTK_MAX_RHS || (n_rhs & (n_rhs - 1)))
         return fail(ctx, FTK_EINVAL, "n_rhs must be a power of two <= 32");
     EpiArgs ea{};
-    return run_hv(ctx, ctx->prec, n_rhs, EPI_PLAIN, v_dev, out_dev, ea);
+    return run_hv(ctx, ctx->mprec, n_rhs, EPI_PLAIN, v_dev, out_dev, ea);
 }
 
 ftk_status ftk_get_vector(ftk_ctx *ctx, int32_t which, double *host_out) {
@@ -745,7 +760,7 @@ ftk_status ftk_get_vector(ftk_ctx *ctx, int32_t which, double *host_out) {
         src = wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * sl);
     }
     void *stage = wsp(ctx, ctx->L.kry[0]);
-    LAUNCH(launch_convert_out(which == 0 ? FTK_FP64 : ctx->prec, src, stage, ctx->dim, scale,
+    LAUNCH(launch_convert_out(which == 0 ? FTK_FP64 : ctx->vprec, src, stage, ctx->dim, scale,
                               vec_grid(ctx, ctx->dim), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(host_out, stage, ctx->dim * 16, cudaMemcpyDeviceToHost));
@@ -756,7 +771,7 @@ ftk_status ftk_plan_info(const ftk_ctx *cctx, int32_t *n_passes, int32_t *tile_b
     ftk_ctx *ctx = const_cast<ftk_ctx *>(cctx);
     if (!ctx) return FTK_EINVAL;
     Plan *pl = nullptr;
-    ftk_status s = get_plan(ctx, ctx->prec, 1, &pl);
+    ftk_status s = get_plan(ctx, ctx->mprec, 1, &pl);
     if (s) return s;
     if (n_passes) *n_passes = (int)pl->passes.size();
     if (tile_bits) *tile_bits = pl->tile_bits;
@@ -766,7 +781,7 @@ ftk_status ftk_plan_info(const ftk_ctx *cctx, int32_t *n_passes, int32_t *tile_b
 ftk_status ftk_suggest_order(int32_t n_sites, const ftk_bond *bonds, int32_t n_bonds, int32_t precision,
                              int32_t n_rhs, int32_t tile_bits, int32_t *perm_out, int32_t *n_passes_out) {
     if (n_sites < 2 || n_sites > FTK_MAX_SITES || !bonds || n_bonds < 1 || n_bonds > 2 * FTK_MAX_PASS_BONDS ||
-        (precision != FTK_FP64 && precision != FTK_FP32) || n_rhs < 1 || n_rhs > FTK_MAX_RHS ||
+        (precision != FTK_FP64 && precision != FTK_FP32 && precision != FTK_MIXED) || n_rhs < 1 || n_rhs > FTK_MAX_RHS ||
         (n_rhs & (n_rhs - 1)) || !perm_out)
         return fail(nullptr, FTK_EINVAL, "ftk_suggest_order: bad arguments");
     PlanBond pb[2 * FTK_MAX_PASS_BONDS];

@@ -25,6 +25,7 @@
 #include "ftk_kernels.h"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace ftk {
 
@@ -128,8 +129,12 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
     }
     const R scale = (EPI == EPI_TPQ) ? (R)(*ea.scale) : (R)1;
     const R ell = (R)ea.ell, inv_n = (R)ea.inv_n;
-    constexpr int ND = (EPI == EPI_TPQ) ? 2 : (EPI == EPI_COCG ? 2 * B : 1);
-    Acc<R> dot[ND];
+    // EPI_COCG_MIXED: the mixed mode's COCG epilogue; its input is the hi part
+    // of a float hi + lo residual and mu is accumulated in double from hi + lo
+    constexpr bool MIX = EPI == EPI_COCG_MIXED;
+    constexpr int ND = (EPI == EPI_TPQ) ? 2 : ((EPI == EPI_COCG || MIX) ? 2 * B : 1);
+    typedef typename std::conditional<MIX, Acc<double>, Acc<R>>::type AccT;
+    AccT dot[ND];
     const bool first = pd.first != 0;
 
     // async copy of a tile of `src` (the thread's own elements) into buf
@@ -238,7 +243,7 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                     dot[0].fma2(pim[k][0], ai[k][0]);
                     dot[1].fma2(yr, yr);
                     dot[1].fma2(yi, yi);
-                } else {
+                } else if (!MIX) {
                     // W = H R;  mu_j = R_j^T W_j (bilinear)
 #pragma unroll
                     for (int j = 0; j < B; ++j) {
@@ -247,6 +252,19 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                         dot[2 * j].fma2(-pim[k][j], ai[k][j]);
                         dot[2 * j + 1].fma2(pr[k][j], ai[k][j]);
                         dot[2 * j + 1].fma2(pim[k][j], ar[k][j]);
+                    }
+                } else {
+                    // mixed mode: R = hi + lo, mu_j = R_j^T W_j in double
+#pragma unroll
+                    for (int j = 0; j < B; ++j) {
+                        ok[(size_t)j * ld] = mk<R>(ar[k][j], ai[k][j]);
+                        const cx lo = reinterpret_cast<const cx *>(ea.lo)[tile_ofs(tau) + eofs(k) + (size_t)j * ld];
+                        const double vr = (double)pr[k][j] + (double)lo.x, vi = (double)pim[k][j] + (double)lo.y;
+                        const double wr = ar[k][j], wi = ai[k][j];
+                        dot[2 * j].fma2(vr, wr);
+                        dot[2 * j].fma2(-vi, wi);
+                        dot[2 * j + 1].fma2(vr, wi);
+                        dot[2 * j + 1].fma2(vi, wr);
                     }
                 }
             }
@@ -429,6 +447,8 @@ template <typename R, int B, int LE>
 static cudaError_t attrs_le() {
     cudaError_t e = opt_in(hv_pass_kernel<R, B, LE, EPI_PLAIN>);
     if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, B, LE, EPI_COCG>);
+    if constexpr (sizeof(R) == 4)
+        if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, B, LE, EPI_COCG_MIXED>);
     if constexpr (B == 1)
         if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, 1, LE, EPI_TPQ>);
     return e;
@@ -468,6 +488,9 @@ static cudaError_t launch_le(int epi, const void *in, void *out, long long ld, c
     void (*k)(const cx *, cx *, long long, const PassDesc, const EpiArgs) = nullptr;
     if (epi == EPI_PLAIN) k = hv_pass_kernel<R, B, LE, EPI_PLAIN>;
     else if (epi == EPI_COCG) k = hv_pass_kernel<R, B, LE, EPI_COCG>;
+    else if constexpr (sizeof(R) == 4) {
+        if (epi == EPI_COCG_MIXED) k = hv_pass_kernel<R, B, LE, EPI_COCG_MIXED>;
+    }
     else if constexpr (B == 1) {
         if (epi == EPI_TPQ) k = hv_pass_kernel<R, 1, LE, EPI_TPQ>;
     }
@@ -522,18 +545,20 @@ static cudaError_t launch_chunk(int bc, int epi, const void *in, void *out, long
 cudaError_t launch_hv_pass(int prec, int B, int epi, const void *in, void *out, const PassDesc &pd,
                            const EpiArgs &ea, int grid_cap, cudaStream_t st) {
     if (B < 1 || (B & (B - 1)) || B > FTK_MAX_RHS || pd.le != hv_le(prec, B, pd.tile_bits, pd.chunk_bits) ||
-        hv_threads(pd) > 512 || (epi == EPI_TPQ && B != 1))
+        hv_threads(pd) > 512 || (epi == EPI_TPQ && B != 1) || (ea.lo && prec == 0))
         return cudaErrorInvalidConfiguration;
     const int bc = std::min(B, hv_max_b(prec));
     const size_t es = prec == 0 ? 16 : 8;
     for (int j0 = 0; j0 < B; j0 += bc) {
         EpiArgs e = ea;
         if (e.result) e.result += 2 * j0;   // COCG: mu of columns j0 .. j0 + bc
+        if (e.lo) e.lo = static_cast<const char *>(e.lo) + (size_t)j0 * (1LL << pd.n_sites) * es;
         const long long ld = 1LL << pd.n_sites;   // column stride: one vector
         const void *i = static_cast<const char *>(in) + (size_t)j0 * ld * es;
         void *o = static_cast<char *>(out) + (size_t)j0 * ld * es;
-        const cudaError_t r = prec == 0 ? launch_chunk<double>(bc, epi, i, o, ld, pd, e, grid_cap, st)
-                                        : launch_chunk<float>(bc, epi, i, o, ld, pd, e, grid_cap, st);
+        const int ep = (epi == EPI_COCG && e.lo && pd.last) ? EPI_COCG_MIXED : epi;
+        const cudaError_t r = prec == 0 ? launch_chunk<double>(bc, ep, i, o, ld, pd, e, grid_cap, st)
+                                        : launch_chunk<float>(bc, ep, i, o, ld, pd, e, grid_cap, st);
         if (r != cudaSuccess) return r;
     }
     return cudaSuccess;

@@ -31,10 +31,50 @@ namespace ftk {
 // lose no digits to the cancellation between z_s r and H r. Fused dots of
 // r_{k+1}: rho = r^T r, g = lambda^dag r, |r|^2 (FTK_UPD_DOTS doubles per RHS).
 // A finished RHS (done != 0) is skipped; its block contributes zeros.
+//
+// Storage policies: plain (R vectors, R arithmetic) and split (the mixed
+// mode: residuals as float hi + lo pairs, hi at p and lo at p + lo_stride,
+// w in float, lambda in double, double arithmetic).
 template <typename R>
-__global__ void __launch_bounds__(256)
-cocg_update_kernel(const typename C2<R>::t *__restrict__ rcur, const typename C2<R>::t *__restrict__ w,
-                   typename C2<R>::t *rprev_new, UpdArgs ua) {
+struct PlainVec {
+    typedef typename C2<R>::t cx;
+    typedef R A;   // arithmetic type
+    const cx *rcur;
+    const cx *w;
+    cx *rnew;
+    __device__ cx load_r(size_t i) const { return rcur[i]; }
+    __device__ cx load_rp(size_t i) const { return rnew[i]; }
+    __device__ cx load_w(size_t i) const { return w[i]; }
+    __device__ void store(size_t i, cx r) const { rnew[i] = r; }
+};
+struct SplitVec {
+    typedef double A;
+    const float2 *rcur;
+    const float2 *w;
+    float2 *rnew;
+    long long lo;
+    __device__ double2 load_r(size_t i) const {
+        const float2 h = rcur[i], l = rcur[i + lo];
+        return make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    }
+    __device__ double2 load_rp(size_t i) const {
+        const float2 h = rnew[i], l = rnew[i + lo];
+        return make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    }
+    __device__ double2 load_w(size_t i) const {
+        const float2 v = w[i];
+        return make_double2((double)v.x, (double)v.y);
+    }
+    __device__ void store(size_t i, double2 r) const {
+        const float hx = (float)r.x, hy = (float)r.y;
+        rnew[i] = make_float2(hx, hy);
+        rnew[i + lo] = make_float2((float)(r.x - (double)hx), (float)(r.y - (double)hy));
+    }
+};
+
+template <typename V>
+__global__ void __launch_bounds__(256) cocg_update_kernel(V vec, UpdArgs ua) {
+    typedef typename V::A R;
     typedef typename C2<R>::t cx;
     __shared__ double red[(256 / 32) * 5];
     if (*ua.all_done) return;
@@ -60,7 +100,7 @@ cocg_update_kernel(const typename C2<R>::t *__restrict__ rcur, const typename C2
             if (ua.mode == 0) {
                 r = l;
             } else {
-                const cx rc = rcur[off + x], wc = w[off + x], rp = rprev_new[off + x];
+                const cx rc = vec.load_r(off + x), wc = vec.load_w(off + x), rp = vec.load_rp(off + x);
                 // A r = z_s r - w
                 R ar = fma(zr_hi, rc.x, -wc.x);
                 ar = fma(-zi_hi, rc.y, ar);
@@ -78,7 +118,7 @@ cocg_update_kernel(const typename C2<R>::t *__restrict__ rcur, const typename C2
                 di = fma(-al_re, ai, di); di = fma(-al_im, ar, di);
                 r = mk<R>(rc.x + dr, rc.y + di);
             }
-            rprev_new[off + x] = r;
+            vec.store(off + x, r);
             d_rr.fma2(r.x, r.x); d_rr.fma2(-r.y, r.y);
             d_ri.fma2(2 * r.x, r.y);
             d_gr.fma2(l.x, r.x); d_gr.fma2(l.y, r.y);
@@ -472,18 +512,23 @@ __global__ void __launch_bounds__(256) spectrum_kernel(SpecArgs sp) {
 }
 
 // ================================================================ launchers
-cudaError_t launch_cocg_update(int prec, int B, const void *rcur, const void *w, void *rprev_new,
+cudaError_t launch_cocg_update(int kind, int B, const void *rcur, const void *w, void *rprev_new,
                                const UpdArgs &ua, int grid, cudaStream_t st) {
     if (B < 1 || B > FTK_MAX_RHS) return cudaErrorInvalidValue;
     const dim3 g(grid, B);
-    if (prec == 0)
-        cocg_update_kernel<double><<<g, 256, 0, st>>>(reinterpret_cast<const double2 *>(rcur),
-                                                      reinterpret_cast<const double2 *>(w),
-                                                      reinterpret_cast<double2 *>(rprev_new), ua);
-    else
-        cocg_update_kernel<float><<<g, 256, 0, st>>>(reinterpret_cast<const float2 *>(rcur),
-                                                     reinterpret_cast<const float2 *>(w),
-                                                     reinterpret_cast<float2 *>(rprev_new), ua);
+    if (kind == 0) {
+        PlainVec<double> v{reinterpret_cast<const double2 *>(rcur), reinterpret_cast<const double2 *>(w),
+                           reinterpret_cast<double2 *>(rprev_new)};
+        cocg_update_kernel<<<g, 256, 0, st>>>(v, ua);
+    } else if (kind == 1) {
+        PlainVec<float> v{reinterpret_cast<const float2 *>(rcur), reinterpret_cast<const float2 *>(w),
+                          reinterpret_cast<float2 *>(rprev_new)};
+        cocg_update_kernel<<<g, 256, 0, st>>>(v, ua);
+    } else {
+        SplitVec v{reinterpret_cast<const float2 *>(rcur), reinterpret_cast<const float2 *>(w),
+                   reinterpret_cast<float2 *>(rprev_new), ua.lo_stride};
+        cocg_update_kernel<<<g, 256, 0, st>>>(v, ua);
+    }
     return cudaGetLastError();
 }
 

@@ -4,7 +4,7 @@
 
 namespace ftk {
 
-enum { EPI_PLAIN = 0, EPI_TPQ = 1, EPI_COCG = 2 };
+enum { EPI_PLAIN = 0, EPI_TPQ = 1, EPI_COCG = 2, EPI_COCG_MIXED = 3 };
 
 struct EpiArgs {
     const double *scale;     // TPQ: device s_k
@@ -15,6 +15,7 @@ struct EpiArgs {
     TpqState *tpq;           // TPQ state (updated by the last block)
     double *stat_u, *stat_logq, *stat_h2;   // TPQ statistics arrays [k]
     const int *all_done;     // COCG: skip when every RHS finished (or NULL)
+    const void *lo;          // COCG, mixed mode: float2 low parts of the input (mu from hi + lo)
 };
 
 struct UpdArgs {
@@ -26,6 +27,7 @@ struct UpdArgs {
     unsigned int *counter;
     double *result;          // [B][FTK_UPD_DOTS]
     const int *all_done;
+    long long lo_stride;     // mixed mode: float2 offset of the lo parts from the hi parts
 };
 
 struct SeedArgs {
@@ -105,7 +107,9 @@ int hv_le(int prec, int B, int tile_bits, int chunk_bits);
 int hv_max_tile_bits(int prec, int B);
 int hv_threads(const PassDesc &pd);
 size_t hv_smem_bytes(int prec, int B, const PassDesc &pd);
-cudaError_t launch_cocg_update(int prec, int B, const void *rcur, const void *w, void *rprev_new,
+// kind: 0 FP64 vectors, 1 FP32 vectors, 2 mixed (split float hi + lo
+// residuals, float w, double lambda)
+cudaError_t launch_cocg_update(int kind, int B, const void *rcur, const void *w, void *rprev_new,
                                const UpdArgs &ua, int grid, cudaStream_t st);
 cudaError_t launch_cocg_seed(const SeedArgs &sa, cudaStream_t st);
 cudaError_t launch_cocg_shift(const ShiftArgs &sh, int n_rhs, cudaStream_t st);
