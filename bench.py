@@ -1,17 +1,21 @@
 """Benchmark of the FTKomega hot path on one GB300 (or N replicas).
 
-Workload (the 24-site plain FP64 FTKomega configuration): periodic honeycomb
-3x4 cells (N = 24, dim 2^24), K = -1, J = 0.05, complex FP64 vectors. One
-step = one pass of the whole hot path over one batch:
-  * 21 mTPQ steps (l = 0.5) from a seeded Philox state, shells at k = 0, 20
+Workload (the 24-site FTKomega configuration at scale): periodic honeycomb
+3x4 cells (N = 24, dim 2^24), K = -1, J = 0.05, sites relabelled by
+ftk_suggest_order. One step = one pass of the whole hot path over one batch:
+  * 21 mTPQ steps (l = 0.5, FP64) from a seeded Philox state, shells k = 0, 20
   * S^z and S^x at momentum Q1 on both shells (4 probes)
-  * one blocked shifted-COCG solve of the 4 probes, 1024 shifts on [-3, 3],
-    eta = 0.01, to the paper's residual 1e-4
+  * one blocked shifted-COCG solve of the 4 probes in the mixed mode (FP32
+    H.V, FP64 Krylov vectors), 1024 shifts on [-3, 3], eta = 0.02, to the
+    paper's residual 1e-4; block plan chosen by ftk_autotune
   * the two spectra (S^z, S^x at Q1) reweighted over the shells to 32
     temperatures in [0.005, 2]
-value = algorithmic H.v bytes of the step (2 * 2^N * 16 B per vector product)
-/ step time, in GB/s ("H.v GB/s"). Spectra/s, per-step latency p50/p99 and
-the roofline of the dominant kernel are reported beside it.
+value = algorithmic H.v bytes of the step (2 * 2^N * s per vector product,
+s = 16 B for the FP64 mTPQ products, 8 B for the FP32 COCG products) / step
+time, in GB/s ("H.v GB/s"). Beside it: spectra/s of this step and of the
+plain FP64 single-vector FTKomega on the same GPU (same seed), the spectrum
+error against that FP64 run, per-step latency p50/p99, and the roofline of
+the dominant kernel (the FP32 H.V of the solve, timed alone).
 
 --impl reference runs the oracle (plain C/OpenMP FP64, test infrastructure)
 on the host cores on a bounded sample of the same workload.
@@ -31,14 +35,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from ftk_inputs import named, omega_grid, log_temperatures  # noqa: E402
+from ftk_inputs import named, omega_grid, log_temperatures, relabel  # noqa: E402
 
 N_SITES = 24
 K_COUPLING, J_COUPLING, ELL = -1.0, 0.05, 0.5
 TPQ_STEPS, SAVE_EVERY = 21, 20
-N_OMEGA, W_MIN, W_MAX, ETA = 1024, -3.0, 3.0, 0.01
+N_OMEGA, W_MIN, W_MAX, ETA = 1024, -3.0, 3.0, 0.02
 N_T = 32
-TOL, MAX_ITER = 1e-4, 10000
+TOL, MAX_ITER = 1e-4, 6000
 METRIC = "H·v GB/s vs HBM peak at N=24; spectra/s at 1e-5 err vs plain FP64; p50/p99"
 
 
@@ -113,6 +117,58 @@ def dist_env():
 
 
 # ---------------------------------------------------------------- GPU arm
+def bench_cluster(n=N_SITES):
+    """The workload's cluster with the site labels that minimise H.v passes
+    (FP32 matvec, one vector per launch)."""
+    import paper_1802_02854_gb300 as ftk
+    cl = named(n)
+    perm, _ = ftk.ftk_suggest_order(n, cl.bonds, ftk.FTK_FP32, 1)
+    return relabel(cl, perm)
+
+
+PROBES = [(0, 2, 1), (1, 2, 1), (0, 0, 1), (1, 0, 1)]   # (shell, gamma, momentum index)
+KINDS = [(2, 1), (0, 1)]                                 # spectra: (gamma, momentum index)
+
+
+def run_step(ctx, cl, omega, temps, seed, sample, slots=None):
+    """mTPQ -> probes -> blocked shifted COCG -> reweighted spectra (one step)."""
+    ctx.tpq_init(seed, sample, ELL)
+    ctx.tpq_step(TPQ_STEPS, SAVE_EVERY)
+    G = np.zeros((len(PROBES), N_OMEGA), dtype=np.complex128)
+    iters = np.zeros(len(PROBES), dtype=np.int64)
+    groups = [list(range(len(PROBES)))] if slots is None else [[p] for p in range(len(PROBES))]
+    for grp in groups:
+        for slot, p in enumerate(grp):
+            sh, g, qi = PROBES[p]
+            ctx.apply_op(sh, g, cl.momenta[qi], slot)
+        Gg, it, st = ctx.shifted_cocg(list(range(len(grp))), omega, ETA, tol=TOL, max_iter=MAX_ITER,
+                                      allow_noconv=True)
+        G[grp] = Gg
+        iters[grp] = it
+    S = [ctx.spectrum(np.stack([G[2 * p], G[2 * p + 1]]), temps)[0] for p in range(len(KINDS))]
+    return iters, G, S
+
+
+def time_hv(ctx, torch, n_rhs, dt, reps=10):
+    """Average time of one H.V (all passes) of n_rhs vectors, CUDA events on
+    the context stream; inputs larger than L2."""
+    import paper_1802_02854_gb300 as ftk
+    v = torch.randn(n_rhs, ctx.dim, dtype=dt, device="cuda")
+    out = torch.empty_like(v)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        ftk.ftk_hv(ctx.handle, v.data_ptr(), out.data_ptr(), n_rhs)
+    ctx.stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(reps):
+        ftk.ftk_hv(ctx.handle, v.data_ptr(), out.data_ptr(), n_rhs)
+    e1.record(ctx.stream)
+    e1.synchronize()
+    del v, out
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
 def run_gpu(args):
     import torch
     import paper_1802_02854_gb300 as ftk
@@ -124,99 +180,98 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     gbuild.build()
-    cl = named(N_SITES)
+    cl = bench_cluster()
     omega = omega_grid(W_MIN, W_MAX, N_OMEGA)
     temps = log_temperatures(0.005, 2.0, N_T)
-    probes = [(0, 2, 1), (1, 2, 1), (0, 0, 1), (1, 0, 1)]   # (shell, gamma, momentum index)
-    kinds = [(2, 1), (0, 1)]                                 # spectra: (gamma, momentum index)
-    n_rhs = len(probes)
-    prec = ftk.FTK_FP64
-    ctx = ftk.Context(cl, K_COUPLING, J_COUPLING, "fp64", max_rhs=n_rhs, n_saved=2)
-    stream = ctx.stream
+    n_rhs = len(PROBES)
     dim = cl.dim
-    hv_bytes_vec = 2 * dim * 16
-
-    def one_step(seed):
-        ctx.tpq_init(seed, rank, ELL)
-        ctx.tpq_step(TPQ_STEPS, SAVE_EVERY)
-        for slot, (sh, g, qi) in enumerate(probes):
-            ctx.apply_op(sh, g, cl.momenta[qi], slot)
-        G, it, st = ctx.shifted_cocg(list(range(n_rhs)), omega, ETA, tol=TOL, max_iter=MAX_ITER,
-                                     allow_noconv=True)
-        S = [ctx.spectrum(np.stack([G[2 * p], G[2 * p + 1]]), temps)[0] for p in range(len(kinds))]
-        return int(np.max(it)), G, S
+    ctx = ftk.Context(cl, K_COUPLING, J_COUPLING, "mixed", max_rhs=n_rhs, n_saved=2)
+    tuned = {"cocg": ctx.autotune(n_rhs, 0), "tpq": ctx.autotune(1, 1)}   # (tile bits, cols, us)
+    stream = ctx.stream
 
     for w in range(args.warmup):
-        one_step(100 + w)
+        run_step(ctx, cl, omega, temps, 100 + w, rank)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     times, iters_tot = [], 0
     l0 = ctx.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    S_mixed = None
     with Clocks() as clk:
         torch.cuda.synchronize()
         for s in range(args.steps):
             ev[s][0].record(stream)
-            it, _, _ = one_step(1000 + s)
+            it, G, S = run_step(ctx, cl, omega, temps, 1000 + s, rank)
             ev[s][1].record(stream)
-            iters_tot += it
+            iters_tot += int(np.max(it))
+            if s == 0:
+                S_mixed = S
         torch.cuda.synchronize()
     launches = ctx.launch_count() - l0
-    for a, b in ev:
-        times.append(a.elapsed_time(b) / 1e3)
+    times = [a.elapsed_time(b) / 1e3 for a, b in ev]
     t_total = sum(times)
     if world > 1:
         import torch.distributed as dist
         tt = torch.tensor([t_total], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt.item())
-    # algorithmic H.v bytes per step: TPQ steps + blocked COCG iterations
-    hv_bytes = args.steps * TPQ_STEPS * hv_bytes_vec + iters_tot * n_rhs * hv_bytes_vec
+    # algorithmic H.v bytes of the steps: FP64 mTPQ products + FP32 COCG products
+    hv_bytes = args.steps * TPQ_STEPS * 2 * dim * 16 + iters_tot * n_rhs * 2 * dim * 8
     value = world * hv_bytes / t_total / 1e9
-    spectra_per_s = world * args.steps * len(kinds) / t_total
+    spectra_per_s = world * args.steps * len(KINDS) / t_total
 
-    # dominant kernel: the blocked H.V of the COCG solve (same plan, same B),
-    # timed alone with CUDA events on the context stream
-    v = torch.randn(n_rhs, dim, dtype=torch.complex128, device="cuda")
-    out = torch.empty_like(v)
-    torch.cuda.synchronize()
-    for _ in range(3):
-        ftk.ftk_hv(ctx.handle, v.data_ptr(), out.data_ptr(), n_rhs)
-    stream.synchronize()
-    reps = 10
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        ftk.ftk_hv(ctx.handle, v.data_ptr(), out.data_ptr(), n_rhs)
-    e1.record(stream)
-    e1.synchronize()
-    t_hv = e0.elapsed_time(e1) / 1e3 / reps
+    # dominant kernel: the FP32 blocked H.V of the solve (autotuned plan), alone
+    t_hv = time_hv(ctx, torch, n_rhs, torch.complex64)
     n_pass, tile_bits = ctx.plan_info()
     peak, peak_kind = peaks()
-    achieved = n_rhs * hv_bytes_vec / t_hv / 1e9
-    del v, out
+    achieved = n_rhs * 2 * dim * 8 / t_hv / 1e9
+    t_hv1 = None
+    ctx1 = ftk.Context(cl, K_COUPLING, J_COUPLING, "fp32", max_rhs=1)
+    t_hv1 = time_hv(ctx1, torch, 1, torch.complex64)
+    p1 = ctx1.plan_info()
+    ctx1.close()
+
+    # plain FP64 single-vector FTKomega on the same GPU, same seed as timed step 0
+    ctx64 = ftk.Context(cl, K_COUPLING, J_COUPLING, "fp64", max_rhs=1, n_saved=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it64, G64, S64 = run_step(ctx64, cl, omega, temps, 1000, rank, slots="single")
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    ctx64.close()
+    errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(S_mixed, S64)]
+    err = max(errs)
 
     # end to end through the public API with host buffers
-    e2e = run_e2e(ctx, cl, omega, temps, probes, kinds, args)
+    e2e = run_e2e(ctx, cl, omega, temps, args)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * t_total / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "honeycomb24 plain FTKw FP64: 3x4 torus, K=-1, J=0.05, dim 2^24; 21 mTPQ steps "
-                               "(shells k=0,20); S^z and S^x at Q1 on both shells = 4 RHS in one blocked "
-                               "COCG; 1024 shifts on [-3,3], eta=0.01, tol 1e-4; 2 spectra x 32 T in [0.005,2]",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 H.v, f64 Krylov vectors/scalars", "data": "synthetic",
+        "config": {"workload": "honeycomb24 FTKw, mixed precision: 3x4 torus, K=-1, J=0.05, dim 2^24; 21 FP64 "
+                               "mTPQ steps (shells k=0,20); S^z and S^x at Q1 on both shells = 4 RHS in one "
+                               "blocked COCG (FP32 H.v, FP64 Krylov vectors); 1024 shifts on [-3,3], eta=0.02, "
+                               "tol 1e-4; 2 spectra x 32 T in [0.005,2]",
                    "n_sites": N_SITES, "n_rhs": n_rhs, "n_omega": N_OMEGA, "n_T": N_T,
-                   "l2": "inputs larger than L2 (256 MiB per vector)", "parallelism": f"replicas{world}"},
+                   "site_order": "ftk_suggest_order", "autotune": tuned,
+                   "l2": "inputs larger than L2 (128-256 MiB per vector)", "parallelism": f"replicas{world}"},
         "spectra_per_s": round(spectra_per_s, 4),
+        "plain_fp64": {"spectra_per_s": round(len(KINDS) / t64, 4), "seconds": round(t64, 3),
+                       "krylov_iters": it64.tolist(), "speedup": round(spectra_per_s / world / (len(KINDS) / t64), 2)},
+        "spectrum_rel_err_vs_fp64": {"max": err, "per_spectrum": errs,
+                                     "norm": "||S - S_fp64||_2 / ||S_fp64||_2 over (omega, T)"},
         "latency_s": {"p50": round(float(np.percentile(times, 50)), 4),
                       "p99": round(float(np.percentile(times, 99)), 4)},
         "krylov_iters_per_step": iters_tot / args.steps,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": f"hv_pass fp64 B={n_rhs} ({n_pass} passes, tile 2^{tile_bits})",
-                     "peak_kind": peak_kind, "hv_us": round(t_hv * 1e6, 2)},
+                     "kernel": f"hv_pass fp32 B={n_rhs} (one H.v = all passes; tile 2^{tuned['cocg'][0]}, "
+                               f"{tuned['cocg'][1]} columns per launch)",
+                     "peak_kind": peak_kind, "hv_us": round(t_hv * 1e6, 2),
+                     "hv_fp32_b1": {"us": round(t_hv1 * 1e6, 2), "gbs": round(2 * dim * 8 / t_hv1 / 1e9, 2),
+                                    "frac": round(2 * dim * 8 / t_hv1 / 1e9 / peak, 4), "passes": p1[0]}},
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -231,34 +286,35 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_e2e(ctx, cl, omega, temps, probes, kinds, args):
-    """Same step through the public API, host state in and host spectra out."""
+def run_e2e(ctx, cl, omega, temps, args):
+    """The same step through the public API with host buffers: the initial
+    state is copied in from pinned host memory, G and the spectra come back
+    to the host (inside the timed region)."""
     import torch
     from ftk_inputs import random_state
 
-    n_rhs = len(probes)
-    psi = random_state(N_SITES, 7)             # host input (pinned copy below)
+    psi = random_state(N_SITES, 7)
     pinned = torch.from_numpy(psi.view(np.float64)).pin_memory()
     host = pinned.numpy().view(np.complex128)
+    n_rhs = len(PROBES)
     torch.cuda.synchronize()
+    n = max(1, min(args.steps, 2))
     t0 = time.perf_counter()
-    hv_iters = 0
-    for s in range(max(1, min(args.steps, 2))):
+    hv_bytes = 0
+    for s in range(n):
         ctx.set_state(host, ELL)
         ctx.tpq_step(TPQ_STEPS, SAVE_EVERY)
-        for slot, (sh, g, qi) in enumerate(probes):
+        for slot, (sh, g, qi) in enumerate(PROBES):
             ctx.apply_op(sh, g, cl.momenta[qi], slot)
         G, it, st = ctx.shifted_cocg(list(range(n_rhs)), omega, ETA, tol=TOL, max_iter=MAX_ITER,
                                      allow_noconv=True)
-        for p in range(len(kinds)):
+        for p in range(len(KINDS)):
             ctx.spectrum(np.stack([G[2 * p], G[2 * p + 1]]), temps)
-        hv_iters += TPQ_STEPS + int(np.max(it)) * n_rhs
+        hv_bytes += TPQ_STEPS * 2 * cl.dim * 16 + int(np.max(it)) * n_rhs * 2 * cl.dim * 8
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    n = max(1, min(args.steps, 2))
-    val = hv_iters * 2 * cl.dim * 16 / dt / 1e9
-    return {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": int(cl.dim * 16),
-            "d2h_bytes_per_step": int(n_rhs * N_OMEGA * 16 + len(kinds) * N_T * N_OMEGA * 8), "steps": n}
+    return {"value": round(hv_bytes / dt / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": int(cl.dim * 16),
+            "d2h_bytes_per_step": int(n_rhs * N_OMEGA * 16 + len(KINDS) * N_T * N_OMEGA * 8), "steps": n}
 
 
 # ------------------------------------------------------------ oracle arm
@@ -315,9 +371,11 @@ def run_hv_only(args):
     from paper_1802_02854_gb300 import build as gbuild
 
     gbuild.build()
-    cl = named(args.hv_sites)
+    cl = bench_cluster(args.hv_sites)
     prec = args.hv_prec
     ctx = ftk.Context(cl, K_COUPLING, J_COUPLING, prec, max_rhs=args.hv_rhs)
+    if args.hv_autotune:
+        ctx.autotune(args.hv_rhs, 0)
     dt = torch.complex128 if prec == "fp64" else torch.complex64
     v = torch.randn(args.hv_rhs, cl.dim, dtype=dt, device="cuda")
     out = torch.empty_like(v)
@@ -340,9 +398,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hv-only", action="store_true", help="only a few H.V launches (profiling)")
     ap.add_argument("--hv-sites", type=int, default=N_SITES)
-    ap.add_argument("--hv-prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--hv-prec", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--hv-rhs", type=int, default=4)
     ap.add_argument("--hv-reps", type=int, default=4)
+    ap.add_argument("--hv-autotune", action="store_true")
     args = ap.parse_args()
     if args.hv_only:
         run_hv_only(args)

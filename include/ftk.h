@@ -200,6 +200,19 @@ ftk_status ftk_plan_info(const ftk_ctx *ctx, int32_t *n_passes, int32_t *tile_bi
 ftk_status ftk_suggest_order(int32_t n_sites, const ftk_bond *bonds, int32_t n_bonds, int32_t precision,
                              int32_t n_rhs, int32_t tile_bits, int32_t *perm_out, int32_t *n_passes_out);
 
+/* Autotuner of the blocked H.V (the batching knob of the Sec. IV.A product
+ * on this hardware). Times, on scratch vectors in the context's Krylov
+ * region, every admissible plan for n_rhs right-hand sides: column chunk
+ * width (1, 2, 4 or 8 vectors per launch) x tile size (the two to three
+ * largest tiles that fit), and installs the fastest one for later ftk_hv,
+ * ftk_shifted_cocg (which = 0, the context's matvec precision) or
+ * ftk_tpq_step (which = 1, FP64, n_rhs = 1) calls. Outputs (may be NULL):
+ * the chosen tile bits and chunk width and its time per H.V in us.
+ * n_rhs: a power of two <= max_rhs. Overwrites the Krylov region (call it
+ * outside a solve). Synchronises. */
+ftk_status ftk_autotune(ftk_ctx *ctx, int32_t n_rhs, int32_t which, int32_t *tile_bits_out, int32_t *cols_out,
+                        double *us_out);
+
 /* Kernel launches issued by this context since creation (for accounting). */
 int64_t ftk_launch_count(const ftk_ctx *ctx);
 

@@ -29,7 +29,7 @@ STATUS_NAMES = ["FTK_OK", "FTK_EINVAL", "FTK_ENOMEM", "FTK_ECUDA", "FTK_ENOCONV"
 EXPORTS = ["ftk_footprint", "ftk_create", "ftk_bind_workspace", "ftk_tpq_init", "ftk_set_state",
            "ftk_tpq_step", "ftk_shells", "ftk_apply_op", "ftk_set_probe", "ftk_shifted_cocg",
            "ftk_spectrum", "ftk_hv", "ftk_get_vector", "ftk_plan_info", "ftk_launch_count",
-           "ftk_last_error", "ftk_destroy", "ftk_tpq_step_noalloc", "ftk_suggest_order"]
+           "ftk_last_error", "ftk_destroy", "ftk_tpq_step_noalloc", "ftk_suggest_order", "ftk_autotune"]
 
 
 class FtkError(RuntimeError):
@@ -89,6 +89,7 @@ def lib() -> C.CDLL:
     L.ftk_destroy.restype = None
     L.ftk_tpq_step_noalloc.argtypes = [i32, C.POINTER(_Bond), i32, dbl, dbl, dbl, vp, vp, pd, vp]
     L.ftk_suggest_order.argtypes = [i32, C.POINTER(_Bond), i32, i32, i32, i32, pi, pi]
+    L.ftk_autotune.argtypes = [vp, i32, i32, pi, pi, pd]
     for name in EXPORTS:
         if name not in ("ftk_footprint", "ftk_launch_count", "ftk_last_error", "ftk_destroy"):
             getattr(L, name).restype = C.c_int
@@ -238,6 +239,16 @@ def ftk_tpq_step_noalloc(n_sites, bonds, K, J, ell, psi_ptr, out_ptr, stream=Non
     return float(st[0]), float(st[1]), float(st[2])
 
 
+def ftk_autotune(ctx, n_rhs, which=0):
+    """Time the admissible H.v plans for n_rhs vectors and install the
+    fastest. Returns (tile_bits, cols, us per H.v)."""
+    tb = C.c_int32()
+    cols = C.c_int32()
+    us = C.c_double()
+    _check(ctx, lib().ftk_autotune(ctx, int(n_rhs), int(which), C.byref(tb), C.byref(cols), C.byref(us)))
+    return tb.value, cols.value, us.value
+
+
 def ftk_suggest_order(n_sites, bonds, precision=FTK_FP64, n_rhs=1, tile_bits=0):
     """Site relabelling for fewer H.v passes: returns (perm, n_passes) with
     site l -> new label perm[l] (apply with ftk_inputs.relabel)."""
@@ -318,6 +329,9 @@ class Context:
 
     def get_vector(self, which):
         return ftk_get_vector(self.handle, which, self.dim)
+
+    def autotune(self, n_rhs=1, which=0):
+        return ftk_autotune(self.handle, n_rhs, which)
 
     def plan_info(self):
         return ftk_plan_info(self.handle)

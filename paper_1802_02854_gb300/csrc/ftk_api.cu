@@ -139,36 +139,34 @@ void ftk::set_thread_error(const char *msg) { g_create_err = msg; }
 
 namespace {
 
-bool plan_passes(ftk_ctx *ctx, int prec, int B, int tile_bits, Plan &pl) {
+// Plan the passes of H.V for column chunks of bc right-hand sides.
+bool plan_passes(ftk_ctx *ctx, int prec, int bc, int tile_bits, Plan &pl) {
     PlanBond pb[2 * FTK_MAX_PASS_BONDS];
     for (int q = 0; q < ctx->nb; ++q) pb[q] = {ctx->bonds[q].i, ctx->bonds[q].j, ctx->bonds[q].g};
     PassDesc pd[FTK_MAX_PASSES];
-    const int np = plan_hv_passes(ctx->n, pb, ctx->nb, ctx->K, ctx->J, elem_bytes(prec), std::min(B, hv_max_b(prec)),
-                                  tile_bits, pd, FTK_MAX_PASSES, &pl.tile_bits, &pl.chunk_bits);
+    const int np = plan_hv_passes(ctx->n, pb, ctx->nb, ctx->K, ctx->J, elem_bytes(prec), bc, tile_bits, pd,
+                                  FTK_MAX_PASSES, &pl.tile_bits, &pl.chunk_bits);
     if (np == 0) return false;
     for (int p = 0; p < np; ++p)
-        if (!hv_layout_pass(pd[p], prec, B)) return false;
+        if (!hv_layout_pass(pd[p], prec, bc)) return false;
     pl.passes.assign(pd, pd + np);
-    return true;
+    pl.threads = hv_threads(pl.passes[0]);
+    pl.smem = hv_smem_bytes(prec, bc, pl.passes[0]);
+    pl.grid = 8 * ctx->n_sm;   // cap of the persistent grid (4 MB of reduction partials)
+    return pl.smem <= (size_t(227) << 10);
 }
 
 ftk_status get_plan(ftk_ctx *ctx, int prec, int B, Plan **out) {
     auto it = ctx->plans.find(prec * 64 + B);
     if (it != ctx->plans.end()) { *out = &it->second; return FTK_OK; }
-    // default: the largest tile (two 64 KB shared-memory buffers per CTA)
-    const int tb_max = hv_max_tile_bits(prec, B);
+    // default: all columns in one launch (at most hv_max_b), the largest tile
+    const int bc = std::min(B, hv_max_b(prec));
+    const int tb_max = hv_max_tile_bits(prec, bc);
     int tb = ctx->tile_bits_req > 0 ? std::min(ctx->tile_bits_req, tb_max) : tb_max;
     tb = std::max(2, std::min(tb, ctx->n));
     Plan pl;
-    if (!plan_passes(ctx, prec, B, tb, pl))
+    if (!plan_passes(ctx, prec, bc, tb, pl))
         return fail(ctx, FTK_EINVAL, "H.v pass planning failed (tile too small for the bond list)");
-    pl.threads = hv_threads(pl.passes[0]);
-    pl.smem = hv_smem_bytes(prec, B, pl.passes[0]);
-    if (pl.smem > (size_t(227) << 10))
-        return fail(ctx, FTK_EINVAL, "tile does not fit in shared memory");
-    // cap of the persistent grid (the launcher trims it to the resident CTAs);
-    // the reduction partials hold 4 MB
-    pl.grid = 8 * ctx->n_sm;
     auto res = ctx->plans.emplace(prec * 64 + B, pl);
     *out = &res.first->second;
     return FTK_OK;
@@ -672,14 +670,21 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     CK(cudaMemcpy(out.data(), d->seed, sizeof(CocgSeed) * B, cudaMemcpyDeviceToHost));
     std::vector<double> g(2 * sa_elems);
     CK(cudaMemcpy(g.data(), G, sa_elems * 16, cudaMemcpyDeviceToHost));
+    std::string why;
     for (int j = 0; j < n_rhs; ++j) {
         memcpy(G_out + size_t(2) * j * n_omega, g.data() + size_t(2) * j * n_omega, sizeof(double) * 2 * n_omega);
         if (iters_out) iters_out[j] = out[j].iters;
-        if (out[j].done == 2 && result == FTK_OK) result = FTK_EBREAKDOWN;
-        if ((out[j].done == 4 || out[j].done == 0) && result == FTK_OK) result = FTK_ENOCONV;
+        const int dn = out[j].done;
+        if ((dn == 2 || dn == 3 || dn == 5) && result != FTK_EBREAKDOWN) {
+            result = FTK_EBREAKDOWN;
+            why = "shifted COCG breakdown (rhs " + std::to_string(j) + ", iteration " + std::to_string(out[j].iters) +
+                  ", " + (dn == 2 ? "r^T r vanished" : dn == 3 ? "alpha denominator vanished" : "non-finite residual") +
+                  ")";
+        }
+        if ((dn == 4 || dn == 0) && result == FTK_OK) result = FTK_ENOCONV;
     }
     if (result == FTK_ENOCONV) ctx->err = "shifted COCG reached max_iter";
-    if (result == FTK_EBREAKDOWN) ctx->err = "shifted COCG breakdown";
+    if (result == FTK_EBREAKDOWN) ctx->err = why;
     return result;
 }
 
@@ -775,6 +780,58 @@ ftk_status ftk_plan_info(const ftk_ctx *cctx, int32_t *n_passes, int32_t *tile_b
     if (s) return s;
     if (n_passes) *n_passes = (int)pl->passes.size();
     if (tile_bits) *tile_bits = pl->tile_bits;
+    return FTK_OK;
+}
+
+ftk_status ftk_autotune(ftk_ctx *ctx, int32_t n_rhs, int32_t which, int32_t *tile_bits_out, int32_t *cols_out,
+                        double *us_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (n_rhs < 1 || n_rhs > ctx->max_rhs || (n_rhs & (n_rhs - 1)) || (which != 0 && which != 1) ||
+        (which == 1 && n_rhs != 1))
+        return fail(ctx, FTK_EINVAL, "ftk_autotune: n_rhs must be a power of two <= max_rhs (1 for which = 1)");
+    const int prec = which == 1 ? 0 : ctx->mprec;
+    const size_t es = elem_bytes(prec);
+    // scratch: two Krylov regions (each max_rhs vectors of the vector precision)
+    void *in = wsp(ctx, ctx->L.kry[0]);
+    void *out = wsp(ctx, ctx->L.kry[1]);
+    CK(cudaMemsetAsync(in, 0, ctx->dim * es * n_rhs, ctx->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best_us = 1e300;
+    Plan best;
+    EpiArgs ea{};
+    ftk_status st = FTK_OK;
+    for (int bc = 1; bc <= std::min((int)n_rhs, hv_max_b(prec)) && st == FTK_OK; bc <<= 1) {
+        const int tb_max = std::min(hv_max_tile_bits(prec, bc), ctx->n);
+        for (int tb = std::max(5, tb_max - 2); tb <= tb_max && st == FTK_OK; ++tb) {
+            Plan pl;
+            if (!plan_passes(ctx, prec, bc, tb, pl)) continue;
+            for (int rep = 0; rep < 4; ++rep) {
+                if (rep == 1 && cudaEventRecord(e0, ctx->stream) != cudaSuccess) st = FTK_ECUDA;
+                for (size_t p = 0; p < pl.passes.size() && st == FTK_OK; ++p)
+                    if (launch_hv_pass(prec, n_rhs, EPI_PLAIN, in, out, pl.passes[p], ea, pl.grid, ctx->stream) !=
+                        cudaSuccess)
+                        st = FTK_ECUDA;
+            }
+            float ms = 0;
+            if (st == FTK_OK && (cudaEventRecord(e1, ctx->stream) != cudaSuccess ||
+                                 cudaEventSynchronize(e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                st = FTK_ECUDA;
+            const double us = 1e3 * ms / 3;
+            if (st == FTK_OK && us < best_us) { best_us = us; best = pl; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != FTK_OK) return fail(ctx, st, "ftk_autotune: CUDA error while timing");
+    if (best.passes.empty()) return fail(ctx, FTK_EINVAL, "ftk_autotune: no admissible plan");
+    ctx->plans[prec * 64 + n_rhs] = best;
+    if (tile_bits_out) *tile_bits_out = best.tile_bits;
+    if (cols_out) *cols_out = best.passes[0].cols;
+    if (us_out) *us_out = best_us;
     return FTK_OK;
 }
 

@@ -51,6 +51,7 @@ struct PassDesc {
     // the register-bit part of the bond mask: 0 none, 1 + a one bit a,
     // 5 + 4a + b two bits a < b.
     int32_t le;
+    int32_t cols;      // right-hand sides per launch (column chunk width)
     int32_t n_groups;
     int32_t grp_tmask[FTK_MAX_PASS_BONDS + 1];
     int32_t grp_end[FTK_MAX_PASS_BONDS + 1];
@@ -87,7 +88,8 @@ struct CocgSeed {
     double nrm;                 // ||r_k||
     double resid;               // last max_s ||r_k|| / |pi^s_k| / ||lambda||
     int32_t k;                  // iteration index of this RHS
-    int32_t done;               // 1 converged, 2 breakdown, 4 max_iter
+    int32_t done;               // 1 converged, 2 r^T r vanished, 3 alpha denominator
+                                // vanished, 4 max_iter, 5 non-finite residual
     int32_t iters;              // iterations accumulated into G
     int32_t pad;
 };

@@ -234,7 +234,7 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                 if (!pd.last || EPI == EPI_PLAIN) {
 #pragma unroll
                     for (int j = 0; j < B; ++j) ok[(size_t)j * ld] = mk<R>(ar[k][j], ai[k][j]);
-                } else if (EPI == EPI_TPQ) {
+                } else if constexpr (EPI == EPI_TPQ) {
                     // psi' = s (l v - H v / N);  <v|Hv>, |psi'|^2
                     const R yr = scale * (ell * pr[k][0] - inv_n * ar[k][0]);
                     const R yi = scale * (ell * pim[k][0] - inv_n * ai[k][0]);
@@ -243,7 +243,7 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                     dot[0].fma2(pim[k][0], ai[k][0]);
                     dot[1].fma2(yr, yr);
                     dot[1].fma2(yi, yi);
-                } else if (!MIX) {
+                } else if constexpr (EPI == EPI_COCG) {
                     // W = H R;  mu_j = R_j^T W_j (bilinear)
 #pragma unroll
                     for (int j = 0; j < B; ++j) {
@@ -253,12 +253,13 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                         dot[2 * j + 1].fma2(pr[k][j], ai[k][j]);
                         dot[2 * j + 1].fma2(pim[k][j], ar[k][j]);
                     }
-                } else {
+                } else if constexpr (MIX) {
                     // mixed mode: R = hi + lo, mu_j = R_j^T W_j in double
 #pragma unroll
                     for (int j = 0; j < B; ++j) {
                         ok[(size_t)j * ld] = mk<R>(ar[k][j], ai[k][j]);
-                        const cx lo = reinterpret_cast<const cx *>(ea.lo)[tile_ofs(tau) + eofs(k) + (size_t)j * ld];
+                        const float2 lo =
+                            reinterpret_cast<const float2 *>(ea.lo)[tile_ofs(tau) + eofs(k) + (size_t)j * ld];
                         const double vr = (double)pr[k][j] + (double)lo.x, vi = (double)pim[k][j] + (double)lo.y;
                         const double wr = ar[k][j], wi = ai[k][j];
                         dot[2 * j].fma2(vr, wr);
@@ -344,6 +345,7 @@ size_t hv_smem_bytes(int prec, int B, const PassDesc &pd) {
 // are renumbered chunk sites, other thread sites, register sites.
 bool hv_layout_pass(PassDesc &pd, int prec, int B) {
     const int b = pd.tile_bits, c = pd.chunk_bits, nb = pd.n_bonds;
+    if (B < 1 || B > hv_max_b(prec) || (B & (B - 1))) return false;
     const int le = hv_le(prec, B, b, c);
     const int tb = b - le;
     // choose the register positions among offset bits [c, b)
@@ -427,6 +429,7 @@ bool hv_layout_pass(PassDesc &pd, int prec, int B) {
     if (w != nb) return false;
     q.n_groups = ng;
     q.le = le;
+    q.cols = B;
     pd = q;
     return true;
 }
@@ -496,7 +499,7 @@ static cudaError_t launch_le(int epi, const void *in, void *out, long long ld, c
     }
     if (!k) return cudaErrorInvalidValue;
     const int threads = hv_threads(pd);
-    const size_t smem = hv_smem_bytes(sizeof(R) == 8 ? 0 : 1, B, pd);
+    const size_t smem = hv_smem_bytes(sizeof(R) == 8 ? 0 : 1, pd.cols, pd);
     // persistent grid: the CTAs that are resident at once
     int per_sm = 0, dev = 0, n_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
@@ -544,10 +547,11 @@ static cudaError_t launch_chunk(int bc, int epi, const void *in, void *out, long
 
 cudaError_t launch_hv_pass(int prec, int B, int epi, const void *in, void *out, const PassDesc &pd,
                            const EpiArgs &ea, int grid_cap, cudaStream_t st) {
-    if (B < 1 || (B & (B - 1)) || B > FTK_MAX_RHS || pd.le != hv_le(prec, B, pd.tile_bits, pd.chunk_bits) ||
-        hv_threads(pd) > 512 || (epi == EPI_TPQ && B != 1) || (ea.lo && prec == 0))
+    const int bc = pd.cols;
+    if (B < 1 || (B & (B - 1)) || B > FTK_MAX_RHS || bc < 1 || bc > hv_max_b(prec) || (B % bc) ||
+        pd.le != hv_le(prec, bc, pd.tile_bits, pd.chunk_bits) || hv_threads(pd) > 512 ||
+        (epi == EPI_TPQ && B != 1) || (ea.lo && prec == 0))
         return cudaErrorInvalidConfiguration;
-    const int bc = std::min(B, hv_max_b(prec));
     const size_t es = prec == 0 ? 16 : 8;
     for (int j0 = 0; j0 < B; j0 += bc) {
         EpiArgs e = ea;

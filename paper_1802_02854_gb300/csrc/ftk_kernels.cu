@@ -101,15 +101,17 @@ __global__ void __launch_bounds__(256) cocg_update_kernel(V vec, UpdArgs ua) {
                 r = l;
             } else {
                 const cx rc = vec.load_r(off + x), wc = vec.load_w(off + x), rp = vec.load_rp(off + x);
-                // A r = z_s r - w
+                // A r = z_s r - w (the lo terms of z_s vanish in double)
                 R ar = fma(zr_hi, rc.x, -wc.x);
                 ar = fma(-zi_hi, rc.y, ar);
-                ar = fma(zr_lo, rc.x, ar);
-                ar = fma(-zi_lo, rc.y, ar);
                 R ai = fma(zr_hi, rc.y, -wc.y);
                 ai = fma(zi_hi, rc.x, ai);
-                ai = fma(zr_lo, rc.y, ai);
-                ai = fma(zi_lo, rc.x, ai);
+                if constexpr (sizeof(R) == 4) {
+                    ar = fma(zr_lo, rc.x, ar);
+                    ar = fma(-zi_lo, rc.y, ar);
+                    ai = fma(zr_lo, rc.y, ai);
+                    ai = fma(zi_lo, rc.x, ai);
+                }
                 // d = c (r - r_prev) - alpha A r
                 const R tr = rc.x - rp.x, ti = rc.y - rp.y;
                 R dr = c_re * tr - c_im * ti;
@@ -202,10 +204,12 @@ __device__ void seed_one(const SeedArgs &sa, CocgSeed &s, int j) {
         if (worst <= sa.tol * s.lnorm) { s.done = 1; return; }
         if (k >= sa.max_iter) { s.done = 4; return; }
     }
-    if (nrm == 0.0 || cabs_(rho) <= 1e-300 * (nrm * nrm) || s.lnorm == 0.0) {
-        s.done = (s.lnorm == 0.0 || nrm == 0.0) ? 1 : 2;
+    if (!isfinite(nrm) || !isfinite(rho.re) || !isfinite(rho.im) || !isfinite(mu.re) || !isfinite(mu.im)) {
+        s.done = 5;   // non-finite residual or dots: breakdown
         return;
     }
+    if (nrm == 0.0 || s.lnorm == 0.0) { s.done = 1; return; }     // exact solution
+    if (cabs_(rho) <= 1e-300 * (nrm * nrm)) { s.done = 2; return; }  // r^T r vanished
     dcx zs = {s.zs_re, s.zs_im};
     dcx beta = {0, 0}, c = {0, 0};
     dcx denom = {cmul(zs, rho).re - mu.re, cmul(zs, rho).im - mu.im};
@@ -215,7 +219,7 @@ __device__ void seed_one(const SeedArgs &sa, CocgSeed &s, int j) {
         dcx t = cdiv(cmul(beta, rho), ap);
         denom.re -= t.re; denom.im -= t.im;
     }
-    if (cabs_(denom) == 0.0) { s.done = 2; return; }
+    if (cabs_(denom) == 0.0) { s.done = 3; return; }
     dcx alpha = cdiv(rho, denom);
     if (k >= 1) {
         dcx ap = {s.alpha_re, s.alpha_im};

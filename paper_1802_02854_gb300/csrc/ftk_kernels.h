@@ -96,9 +96,9 @@ struct SpecArgs {
 cudaError_t init_kernel_attributes();
 void set_thread_error(const char *msg);   // message for ftk_last_error(NULL)
 // H.V pass (ftk_hv.cu). A planned pass is laid out once for the kernel's
-// thread layout (hv_layout_pass) before it is launched; B > hv_max_b(prec)
-// right-hand sides run as column chunks of hv_max_b(prec). grid_cap bounds
-// the persistent grid (the size of ea.partials).
+// thread layout and a column chunk width cols <= hv_max_b(prec)
+// (hv_layout_pass); a launch of B right-hand sides then runs B / cols column
+// chunks. grid_cap bounds the persistent grid (the size of ea.partials).
 cudaError_t launch_hv_pass(int prec, int B, int epi, const void *in, void *out, const PassDesc &pd,
                            const EpiArgs &ea, int grid_cap, cudaStream_t st);
 bool hv_layout_pass(PassDesc &pd, int prec, int B);
