@@ -402,7 +402,11 @@ def main():
     ap.add_argument("--hv-rhs", type=int, default=4)
     ap.add_argument("--hv-reps", type=int, default=4)
     ap.add_argument("--hv-autotune", action="store_true")
+    ap.add_argument("--max-iter", type=int, default=0, help="cap Krylov iterations (profiling runs)")
     args = ap.parse_args()
+    global MAX_ITER
+    if args.max_iter > 0:
+        MAX_ITER = args.max_iter
     if args.hv_only:
         run_hv_only(args)
     elif args.impl == "reference":

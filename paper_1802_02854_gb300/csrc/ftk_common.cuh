@@ -87,6 +87,8 @@ struct CocgSeed {
     double g_re, g_im;          // g_k = lambda^dagger r_k
     double nrm;                 // ||r_k||
     double resid;               // last max_s ||r_k|| / |pi^s_k| / ||lambda||
+    double rescale;             // power of two applied to r_k, r_{k+1}, pi^s in this
+                                // iteration (1: none), keeping ||r|| near ||lambda||
     int32_t k;                  // iteration index of this RHS
     int32_t done;               // 1 converged, 2 r^T r vanished, 3 alpha denominator
                                 // vanished, 4 max_iter, 5 non-finite residual

@@ -25,6 +25,7 @@
 #include "ftk_kernels.h"
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 namespace ftk {
@@ -465,11 +466,9 @@ static cudaError_t attrs_b() {
 }
 
 // Opt every H.V pass instantiation into the full shared memory once per
-// process (outside any stream capture).
-cudaError_t init_kernel_attributes() {
-    static int done = 0;
-    static cudaError_t status = cudaSuccess;
-    if (done) return status;
+// process (outside any stream capture); thread-safe (contexts may be created
+// from several host threads, as the server does).
+static cudaError_t init_attributes_once() {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = attrs_b<double, 1, 3>();
     if (e == cudaSuccess) e = attrs_b<double, 2, 2>();
@@ -479,9 +478,14 @@ cudaError_t init_kernel_attributes() {
     if (e == cudaSuccess) e = attrs_b<float, 2, 3>();
     if (e == cudaSuccess) e = attrs_b<float, 4, 2>();
     if (e == cudaSuccess) e = attrs_b<float, 8, 1>();
-    status = e;
-    done = 1;
     return e;
+}
+
+cudaError_t init_kernel_attributes() {
+    static std::once_flag once;
+    static cudaError_t status = cudaSuccess;
+    std::call_once(once, [] { status = init_attributes_once(); });
+    return status;
 }
 
 template <typename R, int B, int LE>

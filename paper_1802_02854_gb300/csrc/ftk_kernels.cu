@@ -39,17 +39,18 @@ template <typename R>
 struct PlainVec {
     typedef typename C2<R>::t cx;
     typedef R A;   // arithmetic type
-    const cx *rcur;
+    cx *rcur;
     const cx *w;
     cx *rnew;
     __device__ cx load_r(size_t i) const { return rcur[i]; }
     __device__ cx load_rp(size_t i) const { return rnew[i]; }
     __device__ cx load_w(size_t i) const { return w[i]; }
     __device__ void store(size_t i, cx r) const { rnew[i] = r; }
+    __device__ void store_cur(size_t i, cx r) const { rcur[i] = r; }
 };
 struct SplitVec {
     typedef double A;
-    const float2 *rcur;
+    float2 *rcur;
     const float2 *w;
     float2 *rnew;
     long long lo;
@@ -65,11 +66,13 @@ struct SplitVec {
         const float2 v = w[i];
         return make_double2((double)v.x, (double)v.y);
     }
-    __device__ void store(size_t i, double2 r) const {
+    __device__ static void put(float2 *p, long long lo, size_t i, double2 r) {
         const float hx = (float)r.x, hy = (float)r.y;
-        rnew[i] = make_float2(hx, hy);
-        rnew[i + lo] = make_float2((float)(r.x - (double)hx), (float)(r.y - (double)hy));
+        p[i] = make_float2(hx, hy);
+        p[i + lo] = make_float2((float)(r.x - (double)hx), (float)(r.y - (double)hy));
     }
+    __device__ void store(size_t i, double2 r) const { put(rnew, lo, i, r); }
+    __device__ void store_cur(size_t i, double2 r) const { put(rcur, lo, i, r); }
 };
 
 template <typename V>
@@ -91,6 +94,8 @@ __global__ void __launch_bounds__(256) cocg_update_kernel(V vec, UpdArgs ua) {
         c_re = (R)s.c_re; c_im = (R)s.c_im;
     }
     const cx *lam = reinterpret_cast<const cx *>(ua.lambda[j]);
+    // range guard of the seed kernel: r_{k+1} and r_k (the next r_{k-1}) scaled by f
+    const R f = ua.mode == 1 ? (R)ua.seed[j].rescale : (R)1;
     Acc<R> d_rr, d_ri, d_gr, d_gi, d_n;
     if (!skip) {
         for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
@@ -119,6 +124,10 @@ __global__ void __launch_bounds__(256) cocg_update_kernel(V vec, UpdArgs ua) {
                 dr = fma(-al_re, ar, dr); dr = fma(al_im, ai, dr);
                 di = fma(-al_re, ai, di); di = fma(-al_im, ar, di);
                 r = mk<R>(rc.x + dr, rc.y + di);
+                if (f != (R)1) {
+                    r = mk<R>(r.x * f, r.y * f);
+                    vec.store_cur(off + x, mk<R>(rc.x * f, rc.y * f));
+                }
             }
             vec.store(off + x, r);
             d_rr.fma2(r.x, r.x); d_rr.fma2(-r.y, r.y);
@@ -209,7 +218,10 @@ __device__ void seed_one(const SeedArgs &sa, CocgSeed &s, int j) {
         return;
     }
     if (nrm == 0.0 || s.lnorm == 0.0) { s.done = 1; return; }     // exact solution
-    if (cabs_(rho) <= 1e-300 * (nrm * nrm)) { s.done = 2; return; }  // r^T r vanished
+    // r^T r vanished: at a residual 1e-12 below ||lambda|| this is the
+    // underflow of FP32 vectors (the seed system is solved far beyond any
+    // shifted one can still gain): stop as converged; otherwise a breakdown
+    if (cabs_(rho) <= 1e-300 * (nrm * nrm)) { s.done = nrm <= 1e-12 * s.lnorm ? 1 : 2; return; }
     dcx zs = {s.zs_re, s.zs_im};
     dcx beta = {0, 0}, c = {0, 0};
     dcx denom = {cmul(zs, rho).re - mu.re, cmul(zs, rho).im - mu.im};
@@ -225,8 +237,17 @@ __device__ void seed_one(const SeedArgs &sa, CocgSeed &s, int j) {
         dcx ap = {s.alpha_re, s.alpha_im};
         c = cdiv(cmul(beta, alpha), ap);
     }
+    // Range guard: the seed residual can fall many orders below ||lambda||
+    // while slow shifts still converge (their |pi| falls with it); FP32 and
+    // float-pair storage would underflow. Every quantity of the recurrences
+    // is homogeneous in (r, pi), so r_k, r_{k+1} and all pi^s are scaled by
+    // the same power of two f (exact), and the stored rho_k by f^2; the
+    // shifted residuals r / pi^s, alpha, beta, c and G are unchanged.
+    double f = 1.0;
+    if (nrm < 0x1p-40 * s.lnorm) f = ldexp(1.0, ilogb(s.lnorm) - ilogb(nrm));
+    s.rescale = f;
     s.rho_prev_re = s.rho_re; s.rho_prev_im = s.rho_im;
-    s.rho_re = rho.re; s.rho_im = rho.im;
+    s.rho_re = rho.re * f * f; s.rho_im = rho.im * f * f;
     s.alpha_prev_re = s.alpha_re; s.alpha_prev_im = s.alpha_im;
     s.alpha_re = alpha.re; s.alpha_im = alpha.im;
     s.beta_prev_re = beta.re; s.beta_prev_im = beta.im;
@@ -275,6 +296,8 @@ __global__ void cocg_shift_kernel(ShiftArgs sh) {
         dcx as = cdiv(cmul(alpha, pc), pn);
         dcx ag = cmul(as, pt);
         G.re += ag.re; G.im += ag.im;
+        const double f = s.rescale;   // range guard of the seed kernel (1 or a power of two)
+        pc.re *= f; pc.im *= f; pn.re *= f; pn.im *= f;
         sh.pi_prev[o] = pc; sh.pi_cur[o] = pn; sh.ptil[o] = pt; sh.G[o] = G;
         inv_pi = 1.0 / cabs_(pn);
     }
@@ -516,20 +539,20 @@ __global__ void __launch_bounds__(256) spectrum_kernel(SpecArgs sp) {
 }
 
 // ================================================================ launchers
-cudaError_t launch_cocg_update(int kind, int B, const void *rcur, const void *w, void *rprev_new,
+cudaError_t launch_cocg_update(int kind, int B, void *rcur, const void *w, void *rprev_new,
                                const UpdArgs &ua, int grid, cudaStream_t st) {
     if (B < 1 || B > FTK_MAX_RHS) return cudaErrorInvalidValue;
     const dim3 g(grid, B);
     if (kind == 0) {
-        PlainVec<double> v{reinterpret_cast<const double2 *>(rcur), reinterpret_cast<const double2 *>(w),
+        PlainVec<double> v{reinterpret_cast<double2 *>(rcur), reinterpret_cast<const double2 *>(w),
                            reinterpret_cast<double2 *>(rprev_new)};
         cocg_update_kernel<<<g, 256, 0, st>>>(v, ua);
     } else if (kind == 1) {
-        PlainVec<float> v{reinterpret_cast<const float2 *>(rcur), reinterpret_cast<const float2 *>(w),
+        PlainVec<float> v{reinterpret_cast<float2 *>(rcur), reinterpret_cast<const float2 *>(w),
                           reinterpret_cast<float2 *>(rprev_new)};
         cocg_update_kernel<<<g, 256, 0, st>>>(v, ua);
     } else {
-        SplitVec v{reinterpret_cast<const float2 *>(rcur), reinterpret_cast<const float2 *>(w),
+        SplitVec v{reinterpret_cast<float2 *>(rcur), reinterpret_cast<const float2 *>(w),
                    reinterpret_cast<float2 *>(rprev_new), ua.lo_stride};
         cocg_update_kernel<<<g, 256, 0, st>>>(v, ua);
     }

@@ -109,7 +109,7 @@ int hv_threads(const PassDesc &pd);
 size_t hv_smem_bytes(int prec, int B, const PassDesc &pd);
 // kind: 0 FP64 vectors, 1 FP32 vectors, 2 mixed (split float hi + lo
 // residuals, float w, double lambda)
-cudaError_t launch_cocg_update(int kind, int B, const void *rcur, const void *w, void *rprev_new,
+cudaError_t launch_cocg_update(int kind, int B, void *rcur, const void *w, void *rprev_new,
                                const UpdArgs &ua, int grid, cudaStream_t st);
 cudaError_t launch_cocg_seed(const SeedArgs &sa, cudaStream_t st);
 cudaError_t launch_cocg_shift(const ShiftArgs &sh, int n_rhs, cudaStream_t st);

@@ -1,0 +1,288 @@
+"""Continuous-batching server for FTKomega spectrum jobs on one GPU.
+
+Jobs (cluster size N, couplings K and J, probes S^gamma_q, eta, shift grid,
+temperature grid, precision) arrive at any time. A scheduler thread admits a
+waiting job as soon as a slot is free and its device footprint (the
+ftk_footprint workspace plus a fixed allowance for the context's small
+buffers) fits in the memory budget; a job that does not fit lets smaller
+jobs behind it go first (no job is passed over more than `max_skips`
+times). Each admitted job runs on its own CUDA stream in its own worker
+thread with its own context, so the kernels of concurrent jobs overlap on the
+device and later arrivals are admitted as earlier ones finish. A job: mTPQ
+steps from its seeded state (Appendix A), the probes S^gamma_q on every saved
+shell (Sec. V), blocked shifted COCG (probes packed in blocks of `block`
+right-hand sides), reweighting to the temperature grid (Eq. B1, reading R1).
+
+Every number a job returns comes from the CUDA library; the server only
+schedules. A job's arithmetic does not depend on what else runs (own context
+and stream, deterministic reductions), so its result is the same alone and in
+the mix. The scheduler logic takes its runner and footprint functions as
+arguments, so it is testable without a GPU.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+CTX_OVERHEAD_BYTES = 64 << 20   # small device buffers of a context + allocator slack
+
+
+@dataclass
+class JobSpec:
+    """One spectrum job; probes are (gamma, momentum index) pairs, one spectrum each."""
+    n_sites: int
+    K: float = -1.0
+    J: float = 0.1
+    seed: int = 1
+    sample: int = 0
+    ell: float | None = None          # None: max(0.5, l_min)
+    n_steps: int = 21
+    save_every: int = 20
+    probes: list = field(default_factory=lambda: [(2, 1)])
+    omega: tuple = (-3.0, 3.0, 256)   # (min, max, count), endpoints included
+    eta: float = 0.02
+    temps: list = field(default_factory=lambda: [0.1, 0.5, 1.0])
+    precision: str = "fp64"           # "fp64", "fp32" or "mixed"
+    tol: float = 1e-4
+    max_iter: int = 10000
+    block: int = 4
+    cluster: object = None            # prebuilt cluster (default: the named honeycomb torus)
+
+    @property
+    def n_shells(self):
+        return (self.n_steps + self.save_every - 1) // self.save_every
+
+    def footprint(self):
+        from . import PRECISIONS, ftk_footprint
+        return ftk_footprint(self.n_sites, self.n_shells, self.block, PRECISIONS[self.precision]) + CTX_OVERHEAD_BYTES
+
+
+@dataclass
+class JobResult:
+    job_id: int
+    status: str                       # "ok", "noconv", "error: ..."
+    spectra: dict = field(default_factory=dict)   # probe -> S [n_T, n_omega]
+    G: dict = field(default_factory=dict)         # probe -> G [n_shell, n_omega]
+    iters: dict = field(default_factory=dict)     # probe -> iterations per shell
+    trunc: dict = field(default_factory=dict)     # probe -> truncation flags per T
+    arrival: float = 0.0
+    start: float = 0.0
+    finish: float = 0.0
+
+    @property
+    def latency(self):
+        return self.finish - self.arrival
+
+    @property
+    def queue_wait(self):
+        return self.start - self.arrival
+
+
+def ell_for(cl, K, J, ell=None):
+    """l of the job: max(0.5, l_min) unless given; l_min = (1/N) sum_b lambda_max(h_b)
+    with the bond spectrum (J+K)/4 (twice), (J-K)/4, -(3J+K)/4."""
+    lmax = max((J + K) / 4, (J - K) / 4, -(3 * J + K) / 4)
+    lmin = len(cl.bonds) * lmax / cl.n_sites
+    return max(0.5, lmin) if ell is None else ell
+
+
+def run_job(spec: JobSpec, stream=None):
+    """Run one job to completion through the C-ABI (blocking). Returns a
+    dict with spectra, G, iters, trunc and status."""
+    import torch
+
+    from . import FTK_ENOCONV, Context
+    from ftk_inputs import named, omega_grid
+
+    cl = spec.cluster if spec.cluster is not None else named(spec.n_sites)
+    omega = omega_grid(*spec.omega)
+    temps = np.asarray(spec.temps, dtype=np.float64)
+    stream = stream if stream is not None else torch.cuda.Stream()
+    ctx = Context(cl, spec.K, spec.J, spec.precision, max_rhs=spec.block, n_saved=spec.n_shells, stream=stream)
+    try:
+        ctx.tpq_init(spec.seed, spec.sample, ell_for(cl, spec.K, spec.J, spec.ell))
+        ctx.tpq_step(spec.n_steps, spec.save_every)
+        steps, _ = ctx.shells()
+        n_sh = len(steps)
+        # every (probe, shell) is one right-hand side; pack them in blocks
+        rhs = [(p, s) for p in range(len(spec.probes)) for s in range(n_sh)]
+        G = {p: np.zeros((n_sh, len(omega)), dtype=np.complex128) for p in range(len(spec.probes))}
+        iters = {p: np.zeros(n_sh, dtype=np.int64) for p in range(len(spec.probes))}
+        status = "ok"
+        for b0 in range(0, len(rhs), spec.block):
+            blk = rhs[b0:b0 + spec.block]
+            for slot, (p, s) in enumerate(blk):
+                g, qi = spec.probes[p]
+                ctx.apply_op(s, g, cl.momenta[qi], slot)
+            Gb, it, st = ctx.shifted_cocg(list(range(len(blk))), omega, spec.eta, tol=spec.tol,
+                                          max_iter=spec.max_iter, allow_noconv=True)
+            if st == FTK_ENOCONV:
+                status = "noconv"
+            for slot, (p, s) in enumerate(blk):
+                G[p][s] = Gb[slot]
+                iters[p][s] = it[slot]
+        spectra, trunc = {}, {}
+        for p, probe in enumerate(spec.probes):
+            S, tr = ctx.spectrum(G[p], temps)
+            spectra[tuple(probe)] = S
+            trunc[tuple(probe)] = tr
+        return {"status": status, "spectra": spectra, "G": {tuple(spec.probes[p]): G[p] for p in G},
+                "iters": {tuple(spec.probes[p]): iters[p] for p in iters}, "trunc": trunc}
+    finally:
+        ctx.close()
+
+
+class Server:
+    """Admission by footprint, up to max_slots concurrent jobs.
+
+    runner(spec) -> dict (default: run_job on a new stream); footprint(spec)
+    -> bytes (default: spec.footprint()); mem_budget: bytes (default: 90% of
+    the free device memory when the server starts).
+    """
+
+    def __init__(self, max_slots=4, mem_budget=None, runner=None, footprint=None, max_skips=8,
+                 clock=time.perf_counter):
+        self.max_slots = max_slots
+        self.runner = runner or run_job
+        self.footprint = footprint or (lambda s: s.footprint())
+        self.max_skips = max_skips
+        self.clock = clock
+        if mem_budget is None:
+            import torch
+            free, _ = torch.cuda.mem_get_info()
+            mem_budget = int(0.9 * free)
+        self.mem_budget = int(mem_budget)
+        self._lock = threading.Condition()
+        self._pending = deque()           # (job_id, spec, arrival, skips)
+        self._results = {}
+        self._running = {}
+        self._mem_used = 0
+        self._next_id = 0
+        self._closed = False
+        self.peak_running = 0
+        self.peak_mem = 0
+        self.admission_log = []           # (time, job_id, bytes in use after admission)
+        self._sched = threading.Thread(target=self._loop, daemon=True)
+        self._sched.start()
+
+    # ----------------------------------------------------------- public API
+    def submit(self, spec: JobSpec) -> int:
+        need = self.footprint(spec)
+        with self._lock:
+            if self._closed:
+                raise RuntimeError("server closed")
+            jid = self._next_id
+            self._next_id += 1
+            if need > self.mem_budget:
+                now = self.clock()
+                self._results[jid] = JobResult(jid, f"error: footprint {need} B exceeds the budget "
+                                                    f"{self.mem_budget} B", arrival=now, start=now, finish=now)
+            else:
+                self._pending.append([jid, spec, self.clock(), 0])
+            self._lock.notify_all()
+            return jid
+
+    def result(self, job_id, timeout=None) -> JobResult:
+        end = None if timeout is None else self.clock() + timeout
+        with self._lock:
+            while job_id not in self._results:
+                left = None if end is None else end - self.clock()
+                if left is not None and left <= 0:
+                    raise TimeoutError(f"job {job_id} not finished")
+                self._lock.wait(left)
+            return self._results[job_id]
+
+    def drain(self, timeout=None):
+        with self._lock:
+            ids = list(range(self._next_id))
+        return [self.result(j, timeout) for j in ids]
+
+    def stats(self):
+        with self._lock:
+            done = [r for r in self._results.values() if r.status in ("ok", "noconv")]
+            lat = np.array([r.latency for r in done]) if done else np.zeros(0)
+            spectra = sum(len(r.spectra) for r in done)
+            t0 = min((r.arrival for r in done), default=0.0)
+            t1 = max((r.finish for r in done), default=0.0)
+            return {"jobs": len(done), "failed": len(self._results) - len(done), "spectra": spectra,
+                    "spectra_per_s": spectra / (t1 - t0) if t1 > t0 else 0.0,
+                    "latency_p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+                    "latency_p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+                    "peak_running": self.peak_running, "peak_mem_bytes": self.peak_mem,
+                    "mem_budget_bytes": self.mem_budget}
+
+    def close(self):
+        with self._lock:
+            self._closed = True
+            self._lock.notify_all()
+        self._sched.join()
+        for t in list(self._running.values()):
+            t.join()
+
+    # ------------------------------------------------------------ scheduler
+    def _pick(self):
+        """Index of the next pending job to admit, or None. FIFO; a job whose
+        footprint does not fit is skipped (its skip count grows) unless it
+        has been passed over max_skips times, then admission waits for it."""
+        free = self.mem_budget - self._mem_used
+        for i, item in enumerate(self._pending):
+            if self.footprint(item[1]) <= free:
+                return i
+            item[3] += 1
+            if item[3] > self.max_skips:
+                return None
+        return None
+
+    def _loop(self):
+        with self._lock:
+            while True:
+                while not self._closed and (len(self._running) >= self.max_slots or not self._pending or
+                                            self._pick_peek() is None):
+                    self._lock.wait(0.05)
+                if self._closed and not self._pending:
+                    return
+                if self._closed and len(self._running) >= self.max_slots:
+                    self._lock.wait(0.05)
+                    continue
+                i = self._pick()
+                if i is None:
+                    self._lock.wait(0.05)
+                    continue
+                jid, spec, arrival, _ = self._pending[i]
+                del self._pending[i]
+                need = self.footprint(spec)
+                self._mem_used += need
+                self.peak_mem = max(self.peak_mem, self._mem_used)
+                th = threading.Thread(target=self._work, args=(jid, spec, arrival, need), daemon=True)
+                self._running[jid] = th
+                self.peak_running = max(self.peak_running, len(self._running))
+                self.admission_log.append((self.clock(), jid, self._mem_used))
+                th.start()
+
+    def _pick_peek(self):
+        free = self.mem_budget - self._mem_used
+        for item in self._pending:
+            if self.footprint(item[1]) <= free:
+                return item
+            if item[3] >= self.max_skips:
+                return None
+        return None
+
+    def _work(self, jid, spec, arrival, need):
+        start = self.clock()
+        try:
+            out = self.runner(spec)
+            res = JobResult(jid, out.get("status", "ok"), out.get("spectra", {}), out.get("G", {}),
+                            out.get("iters", {}), out.get("trunc", {}))
+        except Exception as e:  # noqa: BLE001 - a failing job must not stop the server
+            res = JobResult(jid, f"error: {type(e).__name__}: {e}")
+        res.arrival, res.start, res.finish = arrival, start, self.clock()
+        with self._lock:
+            self._results[jid] = res
+            self._mem_used -= need
+            del self._running[jid]
+            self._lock.notify_all()

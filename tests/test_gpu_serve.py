@@ -1,0 +1,60 @@
+"""Continuous batching on the GPU: jobs of different cluster sizes,
+couplings, momenta, eta, temperatures and precisions run concurrently on
+their own streams; each result equals the same job run alone, and one job is
+checked against the oracle's eigenbasis estimator. GPU only."""
+import numpy as np
+import pytest
+
+from ftk_inputs import named, omega_grid
+from oracle import dense, sparse
+
+pytestmark = pytest.mark.gpu
+
+
+def _specs(serve):
+    return [
+        serve.JobSpec(n_sites=8, K=-1.0, J=0.1, seed=3, n_steps=31, save_every=10, probes=[(2, 1), (0, 2)],
+                      omega=(-2, 2, 64), eta=0.05, temps=[0.3, 1.0], tol=1e-10, max_iter=3000, block=4),
+        serve.JobSpec(n_sites=10, K=-1.0, J=-0.2, seed=5, n_steps=21, save_every=10, probes=[(1, 0)],
+                      omega=(-3, 3, 100), eta=0.1, temps=[0.5], tol=1e-8, max_iter=3000, block=2),
+        serve.JobSpec(n_sites=12, K=-1.0, J=0.2, seed=9, n_steps=21, save_every=20, probes=[(2, 3), (1, 1)],
+                      omega=(-2, 2, 128), eta=0.1, temps=[0.4, 2.0], tol=1e-6, max_iter=3000, block=4,
+                      precision="fp32"),
+        serve.JobSpec(n_sites=12, K=-1.0, J=0.0, seed=11, n_steps=11, save_every=10, probes=[(2, 2)],
+                      omega=(-2, 2, 64), eta=0.08, temps=[1.0], tol=1e-8, max_iter=3000, block=2,
+                      precision="mixed"),
+    ]
+
+
+def test_alone_equals_mixed_and_matches_oracle():
+    from paper_1802_02854_gb300 import build
+    build.build()
+    from paper_1802_02854_gb300 import serve
+
+    specs = _specs(serve)
+    alone = []
+    for sp in specs:
+        srv = serve.Server(max_slots=1)
+        alone.append(srv.result(srv.submit(sp), timeout=600))
+        srv.close()
+    srv = serve.Server(max_slots=4)
+    ids = [srv.submit(sp) for sp in specs]
+    mixed = [srv.result(j, timeout=600) for j in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["peak_running"] >= 2 and st["latency_p99_s"] >= st["latency_p50_s"] > 0
+    for a, m in zip(alone, mixed):
+        assert a.status == "ok" and m.status == "ok", (a.status, m.status)
+        for key in a.spectra:
+            sa, sm = a.spectra[key], m.spectra[key]
+            assert np.linalg.norm(sa - sm) <= 1e-12 * np.linalg.norm(sa)
+    # job 0 against the oracle's estimator (same seeded Philox state)
+    sp = specs[0]
+    cl = named(8)
+    psi0 = sparse.gaussian_state(8, sp.seed, sp.sample)
+    dg = dense.Diag(cl, sp.K, sp.J)
+    om = omega_grid(*sp.omega)
+    for (g, qi), S in alone[0].spectra.items():
+        ref = dense.dense_estimator(dg, psi0, 0.5, sp.n_steps, sp.save_every, g, cl.momenta[qi], om, sp.eta,
+                                    sp.temps)
+        assert np.linalg.norm(S - ref["S"]) <= 1e-8 * np.linalg.norm(ref["S"])
