@@ -160,6 +160,95 @@ __global__ void __launch_bounds__(256) cocg_update_kernel(V vec, UpdArgs ua) {
     if (threadIdx.x == 0) *ua.counter = 0u;
 }
 
+// Mixed mode, double-float form: the residuals r_k, r_{k-1} (float hi + lo
+// pairs, lo ua.lo_stride float2 after hi) are updated in double-float
+// arithmetic on the FP32 pipe (about 48 bits, the precision of the stored
+// pairs); of the dots, only the one that decides the recurrence keeps double
+// accuracy:
+// rho = r^T r sums the exact double products of the hi parts in double and
+// the small hi x lo cross terms in float. g = lambda^dag r (it enters G
+// linearly) and |r|^2 (the convergence test) use float hi parts with
+// compensated accumulation. lambda is stored in double.
+__global__ void __launch_bounds__(256)
+cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, UpdArgs ua) {
+    __shared__ double red[(256 / 32) * 5];
+    if (*ua.all_done) return;
+    const int j = blockIdx.y;
+    const uint64_t n = ua.dim;
+    const size_t off = (size_t)j * n;
+    const long long lo = ua.lo_stride;
+    const bool skip = ua.mode == 1 && ua.seed[j].done != 0;
+    dcl zs{}, al{}, cc{};
+    float f = 1.f;
+    if (ua.mode == 1) {
+        const CocgSeed &s = ua.seed[j];
+        zs = {dfl_from(s.zs_re), dfl_from(s.zs_im)};
+        al = {dfl_from(s.alpha_re), dfl_from(s.alpha_im)};
+        cc = {dfl_from(s.c_re), dfl_from(s.c_im)};
+        f = (float)s.rescale;   // range guard: a power of two
+    }
+    const double2 *lam = reinterpret_cast<const double2 *>(ua.lambda[j]);
+    double s_rr = 0, s_ri = 0;
+    float c_rr = 0, c_ri = 0;
+    Acc<float> d_gr, d_gi, d_n;
+    if (!skip) {
+        for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+             x += (uint64_t)gridDim.x * blockDim.x) {
+            const double2 ld = lam[x];
+            const float lxr = (float)ld.x, lxi = (float)ld.y;
+            dcl r;
+            const size_t i = off + x;
+            if (ua.mode == 0) {
+                r = {dfl_from(ld.x), dfl_from(ld.y)};
+            } else {
+                const float2 ch = rcur[i], cl = rcur[i + lo], ph = rnew[i], pl = rnew[i + lo], wv = w[i];
+                const dcl rc = {{ch.x, cl.x}, {ch.y, cl.y}};
+                const dcl rp = {{ph.x, pl.x}, {ph.y, pl.y}};
+                // A r = z_s r - w;  r_new = r + c (r - r_prev) - alpha A r
+                dcl ar = dcl_mul(zs, rc);
+                ar.re = dfl_sub(ar.re, {wv.x, 0.f});
+                ar.im = dfl_sub(ar.im, {wv.y, 0.f});
+                r = dcl_add(rc, dcl_sub(dcl_mul(cc, dcl_sub(rc, rp)), dcl_mul(al, ar)));
+                if (f != 1.f) {
+                    r = {{r.re.hi * f, r.re.lo * f}, {r.im.hi * f, r.im.lo * f}};
+                    rcur[i] = make_float2(ch.x * f, ch.y * f);
+                    rcur[i + lo] = make_float2(cl.x * f, cl.y * f);
+                }
+            }
+            rnew[i] = make_float2(r.re.hi, r.im.hi);
+            rnew[i + lo] = make_float2(r.re.lo, r.im.lo);
+            const double xh = r.re.hi, yh = r.im.hi;
+            s_rr = fma(xh, xh, fma(-yh, yh, s_rr));
+            s_ri = fma(2.0 * xh, yh, s_ri);
+            c_rr = fmaf(2.f * r.re.hi, r.re.lo, fmaf(-2.f * r.im.hi, r.im.lo, c_rr));
+            c_ri = fmaf(2.f * r.re.hi, r.im.lo, fmaf(2.f * r.re.lo, r.im.hi, c_ri));
+            d_gr.fma2(lxr, r.re.hi); d_gr.fma2(lxi, r.im.hi);
+            d_gi.fma2(lxr, r.im.hi); d_gi.fma2(-lxi, r.re.hi);
+            d_n.fma2(r.re.hi, r.re.hi); d_n.fma2(r.im.hi, r.im.hi);
+        }
+    }
+    double v[5] = {s_rr + c_rr, s_ri + c_ri, d_gr.get(), d_gi.get(), d_n.get()};
+    block_reduce<5>(v, red);
+    const unsigned nblk = gridDim.x * gridDim.y;
+    double *part = ua.partials + ((size_t)j * gridDim.x + blockIdx.x) * 5;
+    if (threadIdx.x < 5) part[threadIdx.x] = red[threadIdx.x];
+    __shared__ int am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(ua.counter, 1u) == nblk - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    for (int q = threadIdx.x; q < (int)gridDim.y * 5; q += blockDim.x) {
+        const int jj = q / 5, dd = q % 5;
+        double sum = 0.0;
+        for (unsigned bb = 0; bb < gridDim.x; ++bb)
+            sum += __ldcg(ua.partials + ((size_t)jj * gridDim.x + bb) * 5 + dd);
+        ua.result[jj * FTK_UPD_DOTS + dd] = sum;
+    }
+    if (threadIdx.x == 0) *ua.counter = 0u;
+}
+
 // ------------------------------------------------------------ seed scalars
 // One thread per RHS. Reads rho_k, g_k, |r_k| (update kernel) and
 // mu_k = r_k^T H r_k (H pass), the max over shifts of 1/|pi_k| (shift
@@ -551,10 +640,13 @@ cudaError_t launch_cocg_update(int kind, int B, void *rcur, const void *w, void 
         PlainVec<float> v{reinterpret_cast<float2 *>(rcur), reinterpret_cast<const float2 *>(w),
                           reinterpret_cast<float2 *>(rprev_new)};
         cocg_update_kernel<<<g, 256, 0, st>>>(v, ua);
-    } else {
+    } else if (kind == 2) {
         SplitVec v{reinterpret_cast<float2 *>(rcur), reinterpret_cast<const float2 *>(w),
                    reinterpret_cast<float2 *>(rprev_new), ua.lo_stride};
         cocg_update_kernel<<<g, 256, 0, st>>>(v, ua);
+    } else {
+        cocg_update_df_kernel<<<g, 256, 0, st>>>(reinterpret_cast<float2 *>(rcur), reinterpret_cast<const float2 *>(w),
+                                                reinterpret_cast<float2 *>(rprev_new), ua);
     }
     return cudaGetLastError();
 }
