@@ -511,7 +511,7 @@ ftk_status ftk_set_probe(ftk_ctx *ctx, int32_t slot, const double *v, int32_t is
 // Kind of the update kernel: 0 FP64 vectors, 1 FP32 vectors, 2 mixed (split
 // float hi + lo residuals; hi at the buffer start, lo ua.lo_stride float2
 // elements later).
-static int upd_kind(const ftk_ctx *ctx) { return ctx->prec == FTK_MIXED ? 3 : ctx->vprec; }
+static int upd_kind(const ftk_ctx *ctx) { return ctx->prec == FTK_MIXED ? 2 : ctx->vprec; }
 
 static ftk_status cocg_iteration(ftk_ctx *ctx, int B, void *rcur, void *rprev, void *w,
                                  EpiArgs ea, const SeedArgs &sa, const ShiftArgs &sh,

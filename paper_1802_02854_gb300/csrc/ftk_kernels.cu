@@ -32,9 +32,8 @@ namespace ftk {
 // r_{k+1}: rho = r^T r, g = lambda^dag r, |r|^2 (FTK_UPD_DOTS doubles per RHS).
 // A finished RHS (done != 0) is skipped; its block contributes zeros.
 //
-// Storage policies: plain (R vectors, R arithmetic) and split (the mixed
-// mode: residuals as float hi + lo pairs, hi at p and lo at p + lo_stride,
-// w in float, lambda in double, double arithmetic).
+// PlainVec: R vectors and R arithmetic (FP64 and FP32 modes; the mixed mode
+// has its own kernel below).
 template <typename R>
 struct PlainVec {
     typedef typename C2<R>::t cx;
@@ -48,33 +47,6 @@ struct PlainVec {
     __device__ void store(size_t i, cx r) const { rnew[i] = r; }
     __device__ void store_cur(size_t i, cx r) const { rcur[i] = r; }
 };
-struct SplitVec {
-    typedef double A;
-    float2 *rcur;
-    const float2 *w;
-    float2 *rnew;
-    long long lo;
-    __device__ double2 load_r(size_t i) const {
-        const float2 h = rcur[i], l = rcur[i + lo];
-        return make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
-    }
-    __device__ double2 load_rp(size_t i) const {
-        const float2 h = rnew[i], l = rnew[i + lo];
-        return make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
-    }
-    __device__ double2 load_w(size_t i) const {
-        const float2 v = w[i];
-        return make_double2((double)v.x, (double)v.y);
-    }
-    __device__ static void put(float2 *p, long long lo, size_t i, double2 r) {
-        const float hx = (float)r.x, hy = (float)r.y;
-        p[i] = make_float2(hx, hy);
-        p[i + lo] = make_float2((float)(r.x - (double)hx), (float)(r.y - (double)hy));
-    }
-    __device__ void store(size_t i, double2 r) const { put(rnew, lo, i, r); }
-    __device__ void store_cur(size_t i, double2 r) const { put(rcur, lo, i, r); }
-};
-
 template <typename V>
 __global__ void __launch_bounds__(256) cocg_update_kernel(V vec, UpdArgs ua) {
     typedef typename V::A R;
@@ -639,10 +611,6 @@ cudaError_t launch_cocg_update(int kind, int B, void *rcur, const void *w, void 
     } else if (kind == 1) {
         PlainVec<float> v{reinterpret_cast<float2 *>(rcur), reinterpret_cast<const float2 *>(w),
                           reinterpret_cast<float2 *>(rprev_new)};
-        cocg_update_kernel<<<g, 256, 0, st>>>(v, ua);
-    } else if (kind == 2) {
-        SplitVec v{reinterpret_cast<float2 *>(rcur), reinterpret_cast<const float2 *>(w),
-                   reinterpret_cast<float2 *>(rprev_new), ua.lo_stride};
         cocg_update_kernel<<<g, 256, 0, st>>>(v, ua);
     } else {
         cocg_update_df_kernel<<<g, 256, 0, st>>>(reinterpret_cast<float2 *>(rcur), reinterpret_cast<const float2 *>(w),
