@@ -49,7 +49,7 @@ struct PassDesc {
     // sites) and occupy [grp_end[g-1], grp_end[g]); the last group has mask 0
     // (partners held by the thread itself, and the diagonal). bcase encodes
     // the register-bit part of the bond mask: 0 none, 1 + a one bit a,
-    // 5 + 4a + b two bits a < b.
+    // 9 + 8a + b two bits a < b.
     int32_t le;
     int32_t cols;      // right-hand sides per launch (column chunk width)
     int32_t n_groups;

@@ -8,7 +8,8 @@
 // by the tile index; the low offset bits are global bits 0..chunk-1 so every
 // tile is a set of >= 256-byte contiguous runs. Persistent CTAs loop over
 // tiles; the next tile is fetched with cp.async into the second of two
-// shared-memory buffers while the current one is processed.
+// shared-memory buffers while the current one is processed, and the partial
+// product of earlier passes is prefetched into a third.
 //
 // Thread layout: T = 2^tb threads, thread t owns the offsets o = t + T k,
 // k < E = 2^le (register bits = the top le offset bits), with accumulators
@@ -139,9 +140,9 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
     const bool first = pd.first != 0;
 
     // async copy of a tile of `src` (the thread's own elements) into buf
-    auto issue = [&](const cx *src, long tau, cx *buf) {
+    auto issue = [&](const cx *src, long long tofs, cx *buf) {
         if (act) {
-            const cx *g = src + tile_ofs(tau);
+            const cx *g = src + tofs;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 const cx *gk = g + eofs(k);
@@ -156,16 +157,18 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
     // elements it copied itself, so pbuf needs no block barrier.
     const long n_tiles = 1L << pd.n_free;
     long tau = blockIdx.x;
+    long long tofs = tau < n_tiles ? tile_ofs(tau) : 0;
     if (tau < n_tiles) {
-        issue(in, tau, buf0);
-        if (!first) issue(out, tau, pbuf);
+        issue(in, tofs, buf0);
+        if (!first) issue(out, tofs, pbuf);
     }
     for (int it = 0; tau < n_tiles; tau += gridDim.x, ++it) {
         const cx *cur = (it & 1) ? buf1 : buf0;
         cx *nxt = (it & 1) ? buf0 : buf1;
         const long tn = tau + gridDim.x;
         const bool more = tn < n_tiles;
-        if (more) issue(in, tn, nxt);
+        const long long tofs_n = more ? tile_ofs(tn) : 0;
+        if (more) issue(in, tofs_n, nxt);
         // v of this tile: everything but the newest one (first pass) or two groups
         if (first) { if (more) cp_async_wait<1>(); else cp_async_wait<0>(); }
         else { if (more) cp_async_wait<2>(); else cp_async_wait<1>(); }
@@ -199,12 +202,17 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                         FTK_HV_CASE(2, 1, -1)
                         FTK_HV_CASE(3, 2, -1)
                         FTK_HV_CASE(4, 3, -1)
-                        FTK_HV_CASE(5 + 0 * 4 + 1, 0, 1)
-                        FTK_HV_CASE(5 + 0 * 4 + 2, 0, 2)
-                        FTK_HV_CASE(5 + 0 * 4 + 3, 0, 3)
-                        FTK_HV_CASE(5 + 1 * 4 + 2, 1, 2)
-                        FTK_HV_CASE(5 + 1 * 4 + 3, 1, 3)
-                        FTK_HV_CASE(5 + 2 * 4 + 3, 2, 3)
+                        FTK_HV_CASE(5, 4, -1)
+                        FTK_HV_CASE(10, 0, 1)
+                        FTK_HV_CASE(11, 0, 2)
+                        FTK_HV_CASE(12, 0, 3)
+                        FTK_HV_CASE(13, 0, 4)
+                        FTK_HV_CASE(19, 1, 2)
+                        FTK_HV_CASE(20, 1, 3)
+                        FTK_HV_CASE(21, 1, 4)
+                        FTK_HV_CASE(28, 2, 3)
+                        FTK_HV_CASE(29, 2, 4)
+                        FTK_HV_CASE(37, 3, 4)
                         default: break;
                     }
                 }
@@ -228,7 +236,7 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                         ai[k][j] += p.y;
                     }
             }
-            cx *o = out + tile_ofs(tau);
+            cx *o = out + tofs;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 cx *ok = o + eofs(k);
@@ -260,7 +268,7 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                     for (int j = 0; j < B; ++j) {
                         ok[(size_t)j * ld] = mk<R>(ar[k][j], ai[k][j]);
                         const float2 lo =
-                            reinterpret_cast<const float2 *>(ea.lo)[tile_ofs(tau) + eofs(k) + (size_t)j * ld];
+                            reinterpret_cast<const float2 *>(ea.lo)[tofs + eofs(k) + (size_t)j * ld];
                         const double vr = (double)pr[k][j] + (double)lo.x, vi = (double)pim[k][j] + (double)lo.y;
                         const double wr = ar[k][j], wi = ai[k][j];
                         dot[2 * j].fma2(vr, wr);
@@ -271,7 +279,8 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                 }
             }
         }
-        if (!first && more) issue(out, tn, pbuf);
+        if (!first && more) issue(out, tofs_n, pbuf);
+        tofs = tofs_n;
         __syncthreads();   // buffer `cur` is refilled two tiles later
     }
     cp_async_wait<0>();
@@ -303,8 +312,9 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
 
 // ===================================================================== host
 // Register bits per thread: 16 (FP32) or 8 (FP64) amplitude-RHS pairs of
-// accumulators, i.e. le = log2(16 / B) or log2(8 / B). Right-hand-side blocks
-// wider than 8 are processed in column chunks of 8 (register budget).
+// accumulators, i.e. le = log2(16 / B) or log2(8 / B), with at most 512
+// threads per CTA (128 registers). Right-hand-side blocks wider than 8 run
+// in column chunks of 8. (32 pairs with 256 threads measured no faster.)
 static int log2i(int v) {
     int r = 0;
     while ((1 << (r + 1)) <= v) ++r;
@@ -421,7 +431,7 @@ bool hv_layout_pass(PassDesc &pd, int prec, int B) {
             int ka = -1, kb = -1;
             for (int a = 0; a < le; ++a)
                 if ((km >> a) & 1) { if (ka < 0) ka = a; else kb = a; }
-            q.bcase[w] = (int8_t)(ka < 0 ? 0 : kb < 0 ? 1 + ka : 5 + 4 * ka + kb);
+            q.bcase[w] = (int8_t)(ka < 0 ? 0 : kb < 0 ? 1 + ka : 9 + 8 * ka + kb);
             ++w;
         }
         q.grp_tmask[g] = gm[g];
