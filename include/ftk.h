@@ -18,7 +18,9 @@
  *   product), not the FP32 rounding of the recurrence. All scalar inputs and
  *   outputs are double in every mode; norms, inner products, TPQ statistics,
  *   Krylov scalars and reweighting sums are always accumulated in double.
- *   The mTPQ state is FP64 in every mode.
+ *   FTK_DF is the mixed mode with H.v in double-float arithmetic on the FP32
+ *   pipe (hi + lo float pairs in and out, ~48 bits): FP64-class accuracy at
+ *   the FP32 pipe's issue rate. The mTPQ state is FP64 in every mode.
  * Memory: device vectors live in ONE caller-allocated device workspace
  *   (ftk_footprint gives its size, ftk_bind_workspace hands it over); the
  *   library never allocates vector-sized memory itself. The context owns only
@@ -57,7 +59,7 @@ typedef enum {
     FTK_EBUSY = 8         /* context busy / state missing for the request        */
 } ftk_status;
 
-enum { FTK_FP64 = 0, FTK_FP32 = 1, FTK_MIXED = 2 };
+enum { FTK_FP64 = 0, FTK_FP32 = 1, FTK_MIXED = 2, FTK_DF = 3 };
 enum { FTK_GAMMA_X = 0, FTK_GAMMA_Y = 1, FTK_GAMMA_Z = 2 };
 
 /* Cluster geometry: n_sites sites, pos[2*l], pos[2*l+1] = real-space (x, y)
@@ -73,7 +75,7 @@ typedef struct {
 } ftk_bond;
 
 typedef struct {
-    int32_t precision;    /* FTK_FP64, FTK_FP32 or FTK_MIXED                     */
+    int32_t precision;    /* FTK_FP64, FTK_FP32, FTK_MIXED or FTK_DF             */
     int32_t max_rhs;      /* right-hand sides per blocked solve (1..32)          */
     int32_t n_saved;      /* shell states the workspace keeps (>= 1)             */
     int32_t tile_bits;    /* amplitudes per CTA tile = 2^tile_bits; 0 = tuned    */
@@ -175,8 +177,9 @@ ftk_status ftk_spectrum(ftk_ctx *ctx, const double *G, int32_t n_shell, int32_t 
 
 /* out = H v for n_rhs vectors stored one after the other (layout
  * [n_rhs][2^N] complex in the matvec precision: FP64 for FTK_FP64, FP32 for
- * FTK_FP32 and FTK_MIXED; vector j at offset j 2^N). v and out are device
- * pointers, must not overlap, and
+ * FTK_FP32 and FTK_MIXED; vector j at offset j 2^N; for FTK_DF the FP32 hi
+ * parts [n_rhs][2^N] followed by the lo parts [n_rhs][2^N], value hi + lo).
+ * v and out are device pointers, must not overlap, and
  * need 16-byte alignment. The product of Sec. IV.A's cost unit ("a Lanczos
  * step"); exposed for tests and the bandwidth metric. Asynchronous. */
 ftk_status ftk_hv(ftk_ctx *ctx, const void *v_dev, void *out_dev, int32_t n_rhs);

@@ -20,8 +20,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libftk.so")
 
 FTK_OK, FTK_EINVAL, FTK_ENOMEM, FTK_ECUDA, FTK_ENOCONV, FTK_EBREAKDOWN, FTK_ETIMEOUT, FTK_ETRUNC, FTK_EBUSY = range(9)
-FTK_FP64, FTK_FP32, FTK_MIXED = 0, 1, 2
-PRECISIONS = {"fp64": FTK_FP64, "fp32": FTK_FP32, "mixed": FTK_MIXED}
+FTK_FP64, FTK_FP32, FTK_MIXED, FTK_DF = 0, 1, 2, 3
+PRECISIONS = {"fp64": FTK_FP64, "fp32": FTK_FP32, "mixed": FTK_MIXED, "df": FTK_DF}
 STATUS_NAMES = ["FTK_OK", "FTK_EINVAL", "FTK_ENOMEM", "FTK_ECUDA", "FTK_ENOCONV", "FTK_EBREAKDOWN",
                 "FTK_ETIMEOUT", "FTK_ETRUNC", "FTK_EBUSY"]
 
@@ -266,7 +266,8 @@ class Context:
     """A context plus the torch device workspace it runs in.
 
     cluster: object with n_sites, pos [N, 2], bonds [n_bonds, 3].
-    precision: "fp64", "fp32" or "mixed" (FP32 H.v, FP64 Krylov vectors).
+    precision: "fp64", "fp32", "mixed" (FP32 H.v, FP64 Krylov vectors) or "df"
+    (double-float H.v on the FP32 pipe, FP64 Krylov vectors).
     stream: torch.cuda.Stream (default: a new one).
     """
 
@@ -316,9 +317,12 @@ class Context:
 
     def hv(self, v, out=None):
         """v: torch tensor [dim] or [B, dim] (B vectors, one after the other)
-        of complex128/complex64 on cuda."""
+        of complex128/complex64 on cuda; for "df" complex64 [2 B, dim] (the hi
+        parts of the B vectors, then their lo parts)."""
         torch = self.torch
         n_rhs = 1 if v.dim() == 1 else v.shape[0]
+        if self.prec == FTK_DF:
+            n_rhs //= 2
         if out is None:
             out = torch.empty_like(v)
         cur = torch.cuda.current_stream()

@@ -131,7 +131,7 @@ ftk_status fail(ftk_ctx *c, ftk_status s, const std::string &m) {
         ++ctx->launches;    \
     } while (0)
 
-int elem_bytes(int prec) { return prec == FTK_FP64 ? 16 : 8; }
+int elem_bytes(int prec) { return prec == 1 ? 8 : 16; }   // H.v arithmetic: 0 FP64, 1 FP32, 2 double-float
 
 }  // namespace
 
@@ -235,7 +235,7 @@ extern "C" {
 
 size_t ftk_footprint(int32_t n_sites, int32_t n_saved, int32_t max_rhs, int32_t precision) {
     if (n_sites < 2 || n_sites > FTK_MAX_SITES || n_saved < 1 || max_rhs < 1 ||
-        max_rhs > FTK_MAX_RHS || (precision != FTK_FP64 && precision != FTK_FP32 && precision != FTK_MIXED))
+        max_rhs > FTK_MAX_RHS || precision < FTK_FP64 || precision > FTK_DF)
         return 0;
     return make_layout(n_sites, n_saved, max_rhs, precision).total;
 }
@@ -248,8 +248,8 @@ ftk_status ftk_create(const ftk_lattice *lat, const ftk_bond *bonds, int32_t n_b
     const int n = lat->n_sites;
     if (n < 2 || n > FTK_MAX_SITES) return fail(nullptr, FTK_EINVAL, "n_sites must be in [2, 30]");
     if (n_bonds < 1 || n_bonds > 2 * FTK_MAX_PASS_BONDS) return fail(nullptr, FTK_EINVAL, "bad n_bonds");
-    if (opts->precision != FTK_FP64 && opts->precision != FTK_FP32 && opts->precision != FTK_MIXED)
-        return fail(nullptr, FTK_EINVAL, "precision must be FTK_FP64, FTK_FP32 or FTK_MIXED");
+    if (opts->precision < FTK_FP64 || opts->precision > FTK_DF)
+        return fail(nullptr, FTK_EINVAL, "precision must be FTK_FP64, FTK_FP32, FTK_MIXED or FTK_DF");
     if (opts->max_rhs < 1 || opts->max_rhs > FTK_MAX_RHS || opts->n_saved < 1)
         return fail(nullptr, FTK_EINVAL, "max_rhs must be in [1, 32] and n_saved >= 1");
     if (!std::isfinite(K) || !std::isfinite(J)) return fail(nullptr, FTK_EINVAL, "K, J must be finite");
@@ -267,7 +267,7 @@ ftk_status ftk_create(const ftk_lattice *lat, const ftk_bond *bonds, int32_t n_b
     ctx->J = J;
     ctx->prec = opts->precision;
     ctx->vprec = ctx->prec == FTK_FP32 ? 1 : 0;
-    ctx->mprec = ctx->prec == FTK_FP64 ? 0 : 1;
+    ctx->mprec = ctx->prec == FTK_FP64 ? 0 : ctx->prec == FTK_DF ? 2 : 1;
     ctx->max_rhs = opts->max_rhs;
     ctx->n_saved_cap = opts->n_saved;
     ctx->tile_bits_req = opts->tile_bits;
@@ -511,12 +511,13 @@ ftk_status ftk_set_probe(ftk_ctx *ctx, int32_t slot, const double *v, int32_t is
 // Kind of the update kernel: 0 FP64 vectors, 1 FP32 vectors, 2 mixed (split
 // float hi + lo residuals; hi at the buffer start, lo ua.lo_stride float2
 // elements later).
-static int upd_kind(const ftk_ctx *ctx) { return ctx->prec == FTK_MIXED ? 2 : ctx->vprec; }
+static int upd_kind(const ftk_ctx *ctx) { return ctx->prec >= FTK_MIXED ? 2 : ctx->vprec; }
 
 static ftk_status cocg_iteration(ftk_ctx *ctx, int B, void *rcur, void *rprev, void *w,
                                  EpiArgs ea, const SeedArgs &sa, const ShiftArgs &sh,
                                  UpdArgs ua) {
     if (ctx->prec == FTK_MIXED) ea.lo = static_cast<const char *>(rcur) + size_t(8) * ua.lo_stride;
+    if (ctx->prec == FTK_DF) ea.df_lo = ua.lo_stride;   // r and w: lo arrays one region half later
     ftk_status s = run_hv(ctx, ctx->mprec, B, EPI_COCG, rcur, w, ea);
     if (s) return s;
     LAUNCH(launch_cocg_seed(sa, ctx->stream));
@@ -598,7 +599,8 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     ua.counter = &d->counters[3];
     ua.result = d->upd_dots;
     ua.all_done = &d->all_done;
-    ua.lo_stride = (long long)ctx->max_rhs * (long long)ctx->dim;   // mixed mode only
+    ua.lo_stride = (long long)ctx->max_rhs * (long long)ctx->dim;   // mixed and double-float modes
+    ua.w_lo = ctx->prec == FTK_DF ? ua.lo_stride : 0;
     EpiArgs ea{};
     ea.partials = (double *)wsp(ctx, ctx->L.partials);
     ea.counter = &d->counters[4];
@@ -624,7 +626,7 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     sh.tol = tol;
 
     // r_0 = lambda (+ dots); r_{-1} = 0 so that c_0 r_{-1} is exactly zero
-    if (ctx->prec == FTK_MIXED) {   // hi and lo parts of the B columns
+    if (ctx->prec >= FTK_MIXED) {   // hi and lo parts of the B columns
         CK(cudaMemsetAsync(rprev, 0, ctx->dim * 8 * B, ctx->stream));
         CK(cudaMemsetAsync(static_cast<char *>(rprev) + size_t(8) * ua.lo_stride, 0, ctx->dim * 8 * B, ctx->stream));
     } else {
@@ -741,6 +743,7 @@ ftk_status ftk_hv(ftk_ctx *ctx, const void *v_dev, void *out_dev, int32_t n_rhs)
     if (n_rhs < 1 || n_rhs > FTK_MAX_RHS || (n_rhs & (n_rhs - 1)))
         return fail(ctx, FTK_EINVAL, "n_rhs must be a power of two <= 32");
     EpiArgs ea{};
+    if (ctx->mprec == 2) ea.df_lo = (long long)n_rhs * (long long)ctx->dim;   // hi block, then lo block
     return run_hv(ctx, ctx->mprec, n_rhs, EPI_PLAIN, v_dev, out_dev, ea);
 }
 
@@ -802,6 +805,7 @@ ftk_status ftk_autotune(ftk_ctx *ctx, int32_t n_rhs, int32_t which, int32_t *til
     double best_us = 1e300;
     Plan best;
     EpiArgs ea{};
+    if (prec == 2) ea.df_lo = (long long)n_rhs * (long long)ctx->dim;
     ftk_status st = FTK_OK;
     for (int bc = 1; bc <= std::min((int)n_rhs, hv_max_b(prec)) && st == FTK_OK; bc <<= 1) {
         const int tb_max = std::min(hv_max_tile_bits(prec, bc), ctx->n);
@@ -838,7 +842,7 @@ ftk_status ftk_autotune(ftk_ctx *ctx, int32_t n_rhs, int32_t which, int32_t *til
 ftk_status ftk_suggest_order(int32_t n_sites, const ftk_bond *bonds, int32_t n_bonds, int32_t precision,
                              int32_t n_rhs, int32_t tile_bits, int32_t *perm_out, int32_t *n_passes_out) {
     if (n_sites < 2 || n_sites > FTK_MAX_SITES || !bonds || n_bonds < 1 || n_bonds > 2 * FTK_MAX_PASS_BONDS ||
-        (precision != FTK_FP64 && precision != FTK_FP32 && precision != FTK_MIXED) || n_rhs < 1 || n_rhs > FTK_MAX_RHS ||
+        precision < FTK_FP64 || precision > FTK_DF || n_rhs < 1 || n_rhs > FTK_MAX_RHS ||
         (n_rhs & (n_rhs - 1)) || !perm_out)
         return fail(nullptr, FTK_EINVAL, "ftk_suggest_order: bad arguments");
     PlanBond pb[2 * FTK_MAX_PASS_BONDS];
@@ -848,7 +852,7 @@ ftk_status ftk_suggest_order(int32_t n_sites, const ftk_bond *bonds, int32_t n_b
             return fail(nullptr, FTK_EINVAL, "ftk_suggest_order: bond out of range");
         pb[q] = {b.i, b.j, b.gamma};
     }
-    const int prec = precision == FTK_FP64 ? 0 : 1;
+    const int prec = precision == FTK_FP64 ? 0 : precision == FTK_DF ? 2 : 1;
     const int tb_max = hv_max_tile_bits(prec, n_rhs);
     int tb = tile_bits > 0 ? std::min((int)tile_bits, tb_max) : tb_max;
     tb = std::max(2, std::min(tb, (int)n_sites));

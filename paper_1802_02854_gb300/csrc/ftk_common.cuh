@@ -35,12 +35,15 @@ struct PassDesc {
     double anti[FTK_MAX_PASS_BONDS];
     float par_f[FTK_MAX_PASS_BONDS];    // the same in float for the FP32 kernels
     float anti_f[FTK_MAX_PASS_BONDS];
+    float par_lo[FTK_MAX_PASS_BONDS];   // par - par_f, anti - anti_f: low parts of the
+    float anti_lo[FTK_MAX_PASS_BONDS];  // double-float kernel's coefficients
     // The diagonal of a pass is dgv[0] c0 + dgv[1] c1 with integer counts
     // c = sum over the pass's bonds of class dgc (+1 parallel, -1 antiparallel):
     // class 0 = x and y bonds (J/4), class 1 = z bonds ((J + K)/4).
     int32_t dgc[FTK_MAX_PASS_BONDS];
     double dgv[2];
     float dgv_f[2];
+    float dgv_lo[2];
     // Thread layout of the kernel (filled by hv_layout_pass): a CTA of
     // 2^(tile_bits - le) threads, thread t owns the tile offsets t + 2^tb k
     // for k < 2^le (tb = tile_bits - le), i.e. the top le offset bits are

@@ -310,6 +310,217 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
     }
 }
 
+// ------------------------------------------------------------------------
+// Double-float H.V (precision mode FTK_DF): FP64-class accuracy on the FP32
+// pipe, which on GB300 issues 64x the FP64 rate. A vector is a pair of float
+// arrays, hi and lo (lo df_lo float2 elements after hi), value hi + lo
+// (~48 significant bits). The tile holds hi and lo in separate shared-memory
+// arrays; a bond adds c * p with the exact FMA two-product of the hi parts,
+// the cross terms, and Knuth's two-sum into an accumulator (hi, lo) whose lo
+// part collects the rounding errors (renormalised when stored). One column
+// per launch, E = 2^LE amplitudes per thread, same tiling, groups and
+// pipeline as the kernel above.
+__device__ __forceinline__ void df_acc(float &h, float &l, float ch, float cl, float ph, float pl) {
+    const float p = ch * ph;
+    float e = fmaf(ch, ph, -p);
+    e = fmaf(ch, pl, e);
+    e = fmaf(cl, ph, e);
+    const float t = h + p;
+    const float bb = t - h;
+    l += ((h - (t - bb)) + (p - bb)) + e;
+    h = t;
+}
+__device__ __forceinline__ void df_add_to(float &h, float &l, float ph, float pl) {
+    const float t = h + ph;
+    const float bb = t - h;
+    l += ((h - (t - bb)) + (ph - bb)) + pl;
+    h = t;
+}
+
+template <int LE, int KA, int KB>
+__device__ __forceinline__ void bond_apply_df(float (&arh)[1 << LE], float (&arl)[1 << LE], float (&aih)[1 << LE],
+                                              float (&ail)[1 << LE], const float2 (&ph)[1 << LE],
+                                              const float2 (&pl)[1 << LE], float csh, float csl, float cfh,
+                                              float cfl) {
+    constexpr int E = 1 << LE;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int kpar = (KA >= 0 ? (k >> KA) & 1 : 0) ^ (KB >= 0 ? (k >> KB) & 1 : 0);
+        const int kp = k ^ KMask<KA, KB>::m;
+        const float ch = kpar ? cfh : csh, cl = kpar ? cfl : csl;
+        df_acc(arh[k], arl[k], ch, cl, ph[kp].x, pl[kp].x);
+        df_acc(aih[k], ail[k], ch, cl, ph[kp].y, pl[kp].y);
+    }
+}
+
+#define FTK_HV_DF_CASE(ID, KA, KB)                                                                   \
+    case ID:                                                                                         \
+        if constexpr (KA < LE && KB < LE)                                                            \
+            bond_apply_df<LE, KA, KB>(arh, arl, aih, ail, ph, pl, csh, csl, cfh, cfl);               \
+        break;
+
+template <int LE, int EPI>
+__global__ void __launch_bounds__(512, 1)
+hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd, const EpiArgs ea) {
+    constexpr int E = 1 << LE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (ea.all_done && *ea.all_done) return;
+    const long long lo = ea.df_lo;
+    const int b = pd.tile_bits;
+    const int tb = b - LE;
+    const int tile_n = 1 << b;
+    const int T = 1 << tb;
+    const int t = threadIdx.x;
+    const bool act = t < T;
+    float2 *bh0 = reinterpret_cast<float2 *>(smem_raw);
+    float2 *bl0 = bh0 + tile_n, *bh1 = bl0 + tile_n, *bl1 = bh1 + tile_n, *pbh = bl1 + tile_n, *pbl = pbh + tile_n;
+    double *red = reinterpret_cast<double *>(pbl + tile_n);
+
+    uint64_t st = 0;
+    for (int q = 0; q < tb; ++q)
+        if ((t >> q) & 1) st |= 1ull << pd.tile_pos[q];
+    long long kofs[LE > 0 ? LE : 1];
+#pragma unroll
+    for (int q = 0; q < LE; ++q) kofs[q] = (long long)(1ull << pd.tile_pos[tb + q]);
+    auto eofs = [&](int k) -> long long {
+        long long v = (long long)st;
+#pragma unroll
+        for (int q = 0; q < LE; ++q)
+            if ((k >> q) & 1) v += kofs[q];
+        return v;
+    };
+    auto tile_ofs = [&](long tau) -> long long {
+        uint64_t v = 0;
+        for (int q = 0; q < pd.n_free; ++q)
+            if ((tau >> q) & 1) v |= 1ull << pd.free_pos[q];
+        return (long long)v;
+    };
+    // diagonal (double, split once per thread)
+    float dgh[E], dgl[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        double d = 0.0;
+        for (int l = 0; l < pd.n_bonds; ++l) {
+            const int m = (1 << pd.bi[l]) | (1 << pd.bj[l]);
+            const int pt = __popc(t & m & (T - 1)) & 1;
+            const double c = pd.dgv[pd.dgc[l]];
+            d += ((pt ^ __popc(k & (m >> tb))) & 1) ? -c : c;
+        }
+        dgh[k] = (float)d;
+        dgl[k] = (float)(d - (double)dgh[k]);
+    }
+    Acc<double> dot[2];
+    const bool first = pd.first != 0;
+    auto issue = [&](const float2 *src, long long tofs, float2 *bh, float2 *bl) {
+        if (act) {
+            const float2 *g = src + tofs;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const float2 *gk = g + eofs(k);
+                cp_async_elem(bh + t + T * k, gk);
+                cp_async_elem(bl + t + T * k, gk + lo);
+            }
+        }
+        cp_async_commit();
+    };
+    const long n_tiles = 1L << pd.n_free;
+    long tau = blockIdx.x;
+    long long tofs = tau < n_tiles ? tile_ofs(tau) : 0;
+    if (tau < n_tiles) {
+        issue(in, tofs, bh0, bl0);
+        if (!first) issue(out, tofs, pbh, pbl);
+    }
+    for (int it = 0; tau < n_tiles; tau += gridDim.x, ++it) {
+        const float2 *ch = (it & 1) ? bh1 : bh0, *cl = (it & 1) ? bl1 : bl0;
+        float2 *nh = (it & 1) ? bh0 : bh1, *nl = (it & 1) ? bl0 : bl1;
+        const long tn = tau + gridDim.x;
+        const bool more = tn < n_tiles;
+        const long long tofs_n = more ? tile_ofs(tn) : 0;
+        if (more) issue(in, tofs_n, nh, nl);
+        if (first) { if (more) cp_async_wait<1>(); else cp_async_wait<0>(); }
+        else { if (more) cp_async_wait<2>(); else cp_async_wait<1>(); }
+        __syncthreads();
+        if (act) {
+            float arh[E], arl[E], aih[E], ail[E];
+            float2 ph[E], pl[E];
+#pragma unroll
+            for (int k = 0; k < E; ++k) { arh[k] = 0.f; arl[k] = 0.f; aih[k] = 0.f; ail[k] = 0.f; }
+            int q = 0;
+            for (int g = 0; g < pd.n_groups; ++g) {
+                const int tm = pd.grp_tmask[g];
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    ph[k] = ch[(t ^ tm) + T * k];
+                    pl[k] = cl[(t ^ tm) + T * k];
+                }
+                const int pt = __popc(t & tm) & 1;
+                for (const int end = pd.grp_end[g]; q < end; ++q) {
+                    const float parh = pd.par_f[q], parl = pd.par_lo[q], anth = pd.anti_f[q], antl = pd.anti_lo[q];
+                    const float csh = pt ? anth : parh, csl = pt ? antl : parl;
+                    const float cfh = pt ? parh : anth, cfl = pt ? parl : antl;
+                    switch (pd.bcase[q]) {
+                        FTK_HV_DF_CASE(0, -1, -1)
+                        FTK_HV_DF_CASE(1, 0, -1)
+                        FTK_HV_DF_CASE(2, 1, -1)
+                        FTK_HV_DF_CASE(3, 2, -1)
+                        FTK_HV_DF_CASE(4, 3, -1)
+                        FTK_HV_DF_CASE(9 + 0 * 8 + 1, 0, 1)
+                        FTK_HV_DF_CASE(9 + 0 * 8 + 2, 0, 2)
+                        FTK_HV_DF_CASE(9 + 0 * 8 + 3, 0, 3)
+                        FTK_HV_DF_CASE(9 + 1 * 8 + 2, 1, 2)
+                        FTK_HV_DF_CASE(9 + 1 * 8 + 3, 1, 3)
+                        FTK_HV_DF_CASE(9 + 2 * 8 + 3, 2, 3)
+                        default: break;
+                    }
+                }
+            }
+            // own amplitudes (last group): diagonal
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                df_acc(arh[k], arl[k], dgh[k], dgl[k], ph[k].x, pl[k].x);
+                df_acc(aih[k], ail[k], dgh[k], dgl[k], ph[k].y, pl[k].y);
+            }
+            if (!first) {
+                if (more) cp_async_wait<1>(); else cp_async_wait<0>();
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const float2 h = pbh[t + T * k], l = pbl[t + T * k];
+                    df_add_to(arh[k], arl[k], h.x, l.x);
+                    df_add_to(aih[k], ail[k], h.y, l.y);
+                }
+            }
+            float2 *o = out + tofs;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                // renormalise (fast two-sum) and store hi, lo
+                const float rh = arh[k] + arl[k], rl = arl[k] - (rh - arh[k]);
+                const float ih = aih[k] + ail[k], il = ail[k] - (ih - aih[k]);
+                float2 *ok = o + eofs(k);
+                ok[0] = make_float2(rh, ih);
+                ok[lo] = make_float2(rl, il);
+                if (EPI == EPI_COCG && pd.last) {
+                    // mu = r^T w (bilinear) in double from hi + lo
+                    const double vr = (double)ph[k].x + (double)pl[k].x, vi = (double)ph[k].y + (double)pl[k].y;
+                    const double wr = (double)rh + (double)rl, wi = (double)ih + (double)il;
+                    dot[0].fma2(vr, wr);
+                    dot[0].fma2(-vi, wi);
+                    dot[1].fma2(vr, wi);
+                    dot[1].fma2(vi, wr);
+                }
+            }
+        }
+        if (!first && more) issue(out, tofs_n, pbh, pbl);
+        tofs = tofs_n;
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+    if (EPI != EPI_COCG || !pd.last) return;
+    double v[2] = {dot[0].get(), dot[1].get()};
+    block_reduce<2>(v, red);
+    if (threadIdx.x < 2) ea.partials[(size_t)blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
+    last_block_reduce<2>(ea.partials, ea.counter, ea.result, red);
+}
+
 // ===================================================================== host
 // Register bits per thread: 16 (FP32) or 8 (FP64) amplitude-RHS pairs of
 // accumulators, i.e. le = log2(16 / B) or log2(8 / B), with at most 512
@@ -320,10 +531,10 @@ static int log2i(int v) {
     while ((1 << (r + 1)) <= v) ++r;
     return r;
 }
-int hv_max_b(int prec) { (void)prec; return 8; }
+int hv_max_b(int prec) { return prec == 2 ? 1 : 8; }
 static int hv_le_default(int prec, int B) {
     const int bc = std::min(B, hv_max_b(prec));
-    return std::max(0, (prec == 0 ? 3 : 4) - log2i(bc));
+    return std::max(0, (prec == 1 ? 4 : 3) - log2i(bc));
 }
 int hv_le(int prec, int B, int tile_bits, int chunk_bits) {
     const int le = hv_le_default(prec, B);
@@ -334,7 +545,7 @@ int hv_le(int prec, int B, int tile_bits, int chunk_bits) {
 // for the partial product) and at most 512 threads.
 int hv_max_tile_bits(int prec, int B) {
     const int bc = std::min(B, hv_max_b(prec));
-    const int es = prec == 0 ? 16 : 8;
+    const int es = prec == 1 ? 8 : 16;   // FP64 and double-float: 16 B per amplitude
     int tb = 0;
     while ((size_t(2) << tb) * bc * es <= (size_t(64) << 10)) ++tb;
     return std::min(tb, 9 + hv_le_default(prec, B));
@@ -345,7 +556,7 @@ int hv_threads(const PassDesc &pd) {
 }
 size_t hv_smem_bytes(int prec, int B, const PassDesc &pd) {
     const int bc = std::min(B, hv_max_b(prec));
-    const size_t es = prec == 0 ? 16 : 8;
+    const size_t es = prec == 1 ? 8 : 16;
     const int nd = std::max(2, 2 * bc);
     return size_t(3) * ((size_t)1 << pd.tile_bits) * bc * es + (size_t)(hv_threads(pd) / 32) * nd * 8;
 }
@@ -426,6 +637,8 @@ bool hv_layout_pass(PassDesc &pd, int prec, int B) {
             q.anti[w] = pd.anti[l];
             q.par_f[w] = pd.par_f[l];
             q.anti_f[w] = pd.anti_f[l];
+            q.par_lo[w] = pd.par_lo[l];
+            q.anti_lo[w] = pd.anti_lo[l];
             q.dgc[w] = pd.dgc[l];
             const int km = ((1 << bi) | (1 << bj)) >> tb;
             int ka = -1, kb = -1;
@@ -478,8 +691,17 @@ static cudaError_t attrs_b() {
 // Opt every H.V pass instantiation into the full shared memory once per
 // process (outside any stream capture); thread-safe (contexts may be created
 // from several host threads, as the server does).
+template <int LE>
+static cudaError_t attrs_df() {
+    cudaError_t e = opt_in(hv_pass_df_kernel<LE, EPI_PLAIN>);
+    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_COCG>);
+    return e;
+}
+
 static cudaError_t init_attributes_once() {
     cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = attrs_df<3>();
+    if (e == cudaSuccess) e = attrs_df<0>();
     if (e == cudaSuccess) e = attrs_b<double, 1, 3>();
     if (e == cudaSuccess) e = attrs_b<double, 2, 2>();
     if (e == cudaSuccess) e = attrs_b<double, 4, 1>();
@@ -559,13 +781,51 @@ static cudaError_t launch_chunk(int bc, int epi, const void *in, void *out, long
     }
 }
 
+template <int LE>
+static cudaError_t launch_df_le(int epi, const void *in, void *out, const PassDesc &pd, const EpiArgs &ea,
+                                int grid_cap, cudaStream_t st) {
+    void (*k)(const float2 *, float2 *, const PassDesc, const EpiArgs) =
+        epi == EPI_COCG ? hv_pass_df_kernel<LE, EPI_COCG> : hv_pass_df_kernel<LE, EPI_PLAIN>;
+    const int threads = hv_threads(pd);
+    const size_t smem = hv_smem_bytes(2, 1, pd);
+    int per_sm = 0, dev = 0, n_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long g = std::min<long>((long)per_sm * n_sm, 1L << pd.n_free);
+    if (g > grid_cap) g = grid_cap;
+    k<<<(int)g, threads, smem, st>>>(reinterpret_cast<const float2 *>(in), reinterpret_cast<float2 *>(out), pd, ea);
+    return cudaGetLastError();
+}
+
+// Double-float passes: B columns, one launch each; column j's hi array at
+// j 2^N, its lo array ea.df_lo float2 later (both for in and out).
+static cudaError_t launch_hv_pass_df(int B, int epi, const void *in, void *out, const PassDesc &pd,
+                                     const EpiArgs &ea, int grid_cap, cudaStream_t st) {
+    if (epi != EPI_PLAIN && epi != EPI_COCG) return cudaErrorInvalidValue;
+    const long long ld = 1LL << pd.n_sites;
+    for (int j = 0; j < B; ++j) {
+        EpiArgs e = ea;
+        if (e.result) e.result += 2 * j;
+        const void *i = static_cast<const float2 *>(in) + (size_t)j * ld;
+        void *o = static_cast<float2 *>(out) + (size_t)j * ld;
+        const cudaError_t r = pd.le == 3 ? launch_df_le<3>(epi, i, o, pd, e, grid_cap, st)
+                                         : launch_df_le<0>(epi, i, o, pd, e, grid_cap, st);
+        if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_hv_pass(int prec, int B, int epi, const void *in, void *out, const PassDesc &pd,
                            const EpiArgs &ea, int grid_cap, cudaStream_t st) {
     const int bc = pd.cols;
     if (B < 1 || (B & (B - 1)) || B > FTK_MAX_RHS || bc < 1 || bc > hv_max_b(prec) || (B % bc) ||
         pd.le != hv_le(prec, bc, pd.tile_bits, pd.chunk_bits) || hv_threads(pd) > 512 ||
-        (epi == EPI_TPQ && B != 1) || (ea.lo && prec == 0))
+        (epi == EPI_TPQ && B != 1) || (ea.lo && prec != 1) || (prec == 2 && ea.df_lo <= 0))
         return cudaErrorInvalidConfiguration;
+    if (prec == 2) return launch_hv_pass_df(B, epi, in, out, pd, ea, grid_cap, st);
     const size_t es = prec == 0 ? 16 : 8;
     for (int j0 = 0; j0 < B; j0 += bc) {
         EpiArgs e = ea;

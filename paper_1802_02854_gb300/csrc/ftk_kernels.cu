@@ -132,15 +132,15 @@ __global__ void __launch_bounds__(256) cocg_update_kernel(V vec, UpdArgs ua) {
     if (threadIdx.x == 0) *ua.counter = 0u;
 }
 
-// Mixed mode, double-float form: the residuals r_k, r_{k-1} (float hi + lo
-// pairs, lo ua.lo_stride float2 after hi) are updated in double-float
+// Mixed and double-float modes: the residuals r_k, r_{k-1} (float hi + lo
+// pairs, lo ua.lo_stride float2 after hi; w is float, or a pair with its lo
+// ua.w_lo float2 after hi in the double-float mode) are updated in double-float
 // arithmetic on the FP32 pipe (about 48 bits, the precision of the stored
 // pairs); of the dots, only the one that decides the recurrence keeps double
-// accuracy:
-// rho = r^T r sums the exact double products of the hi parts in double and
-// the small hi x lo cross terms in float. g = lambda^dag r (it enters G
-// linearly) and |r|^2 (the convergence test) use float hi parts with
-// compensated accumulation. lambda is stored in double.
+// accuracy: rho = r^T r and g = lambda^dag r sum the exact double products
+// of the hi parts in double and the small hi x lo cross terms in float;
+// |r|^2 (the convergence test) uses the hi parts with compensated float
+// accumulation. lambda is stored in double.
 __global__ void __launch_bounds__(256)
 cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, UpdArgs ua) {
     __shared__ double red[(256 / 32) * 5];
@@ -160,26 +160,28 @@ cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, 
         f = (float)s.rescale;   // range guard: a power of two
     }
     const double2 *lam = reinterpret_cast<const double2 *>(ua.lambda[j]);
-    double s_rr = 0, s_ri = 0;
-    float c_rr = 0, c_ri = 0;
-    Acc<float> d_gr, d_gi, d_n;
+    double s_rr = 0, s_ri = 0, s_gr = 0, s_gi = 0;
+    float c_rr = 0, c_ri = 0, c_gr = 0, c_gi = 0;
+    Acc<float> d_n;
     if (!skip) {
         for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
              x += (uint64_t)gridDim.x * blockDim.x) {
             const double2 ld = lam[x];
             const float lxr = (float)ld.x, lxi = (float)ld.y;
+            const float lxr_lo = (float)(ld.x - (double)lxr), lxi_lo = (float)(ld.y - (double)lxi);
             dcl r;
             const size_t i = off + x;
             if (ua.mode == 0) {
                 r = {dfl_from(ld.x), dfl_from(ld.y)};
             } else {
                 const float2 ch = rcur[i], cl = rcur[i + lo], ph = rnew[i], pl = rnew[i + lo], wv = w[i];
+                const float2 wl = ua.w_lo ? w[i + ua.w_lo] : make_float2(0.f, 0.f);   // double-float w
                 const dcl rc = {{ch.x, cl.x}, {ch.y, cl.y}};
                 const dcl rp = {{ph.x, pl.x}, {ph.y, pl.y}};
                 // A r = z_s r - w;  r_new = r + c (r - r_prev) - alpha A r
                 dcl ar = dcl_mul(zs, rc);
-                ar.re = dfl_sub(ar.re, {wv.x, 0.f});
-                ar.im = dfl_sub(ar.im, {wv.y, 0.f});
+                ar.re = dfl_sub(ar.re, {wv.x, wl.x});
+                ar.im = dfl_sub(ar.im, {wv.y, wl.y});
                 r = dcl_add(rc, dcl_sub(dcl_mul(cc, dcl_sub(rc, rp)), dcl_mul(al, ar)));
                 if (f != 1.f) {
                     r = {{r.re.hi * f, r.re.lo * f}, {r.im.hi * f, r.im.lo * f}};
@@ -194,12 +196,16 @@ cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, 
             s_ri = fma(2.0 * xh, yh, s_ri);
             c_rr = fmaf(2.f * r.re.hi, r.re.lo, fmaf(-2.f * r.im.hi, r.im.lo, c_rr));
             c_ri = fmaf(2.f * r.re.hi, r.im.lo, fmaf(2.f * r.re.lo, r.im.hi, c_ri));
-            d_gr.fma2(lxr, r.re.hi); d_gr.fma2(lxi, r.im.hi);
-            d_gi.fma2(lxr, r.im.hi); d_gi.fma2(-lxi, r.re.hi);
+            // g = lambda^dag r: exact hi x hi products in double, cross terms in float
+            const double lx = lxr, ly = lxi;
+            s_gr = fma(lx, xh, fma(ly, yh, s_gr));
+            s_gi = fma(lx, yh, fma(-ly, xh, s_gi));
+            c_gr = fmaf(lxr, r.re.lo, fmaf(lxr_lo, r.re.hi, fmaf(lxi, r.im.lo, fmaf(lxi_lo, r.im.hi, c_gr))));
+            c_gi = fmaf(lxr, r.im.lo, fmaf(lxr_lo, r.im.hi, fmaf(-lxi, r.re.lo, fmaf(-lxi_lo, r.re.hi, c_gi))));
             d_n.fma2(r.re.hi, r.re.hi); d_n.fma2(r.im.hi, r.im.hi);
         }
     }
-    double v[5] = {s_rr + c_rr, s_ri + c_ri, d_gr.get(), d_gi.get(), d_n.get()};
+    double v[5] = {s_rr + c_rr, s_ri + c_ri, s_gr + c_gr, s_gi + c_gi, d_n.get()};
     block_reduce<5>(v, red);
     const unsigned nblk = gridDim.x * gridDim.y;
     double *part = ua.partials + ((size_t)j * gridDim.x + blockIdx.x) * 5;

@@ -16,6 +16,7 @@ struct EpiArgs {
     double *stat_u, *stat_logq, *stat_h2;   // TPQ statistics arrays [k]
     const int *all_done;     // COCG: skip when every RHS finished (or NULL)
     const void *lo;          // COCG, mixed mode: float2 low parts of the input (mu from hi + lo)
+    long long df_lo;         // double-float mode: float2 offset of the lo arrays of in and out
 };
 
 struct UpdArgs {
@@ -27,7 +28,8 @@ struct UpdArgs {
     unsigned int *counter;
     double *result;          // [B][FTK_UPD_DOTS]
     const int *all_done;
-    long long lo_stride;     // mixed mode: float2 offset of the lo parts from the hi parts
+    long long lo_stride;     // mixed / double-float: float2 offset of the lo parts from the hi parts
+    long long w_lo;          // double-float mode: float2 offset of w's lo part (0: w is float)
 };
 
 struct SeedArgs {

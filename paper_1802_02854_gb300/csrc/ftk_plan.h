@@ -142,6 +142,8 @@ inline int plan_hv_passes(int n, const PlanBond *bonds, int nb, double K, double
             p.anti[taken] = anti;
             p.par_f[taken] = (float)par;
             p.anti_f[taken] = (float)anti;
+            p.par_lo[taken] = (float)(par - (double)p.par_f[taken]);
+            p.anti_lo[taken] = (float)(anti - (double)p.anti_f[taken]);
             p.dgc[taken] = bonds[q].g == 2 ? 1 : 0;
             remaining[q] = 0;
             ++taken;
@@ -152,6 +154,8 @@ inline int plan_hv_passes(int n, const PlanBond *bonds, int nb, double K, double
         p.dgv[1] = (J + K) / 4;
         p.dgv_f[0] = (float)p.dgv[0];
         p.dgv_f[1] = (float)p.dgv[1];
+        p.dgv_lo[0] = (float)(p.dgv[0] - (double)p.dgv_f[0]);
+        p.dgv_lo[1] = (float)(p.dgv[1] - (double)p.dgv_f[1]);
         ++np;
     }
     for (int q = 0; q < nb; ++q)

@@ -12,7 +12,7 @@ from oracle import dense, sparse
 pytestmark = pytest.mark.gpu
 
 TOL_HV = {"fp64": 1e-12, "fp32": 1e-6}
-TOL_S = {"fp64": 1e-8, "fp32": 1e-5, "mixed": 1e-5}
+TOL_S = {"fp64": 1e-8, "fp32": 1e-5, "mixed": 1e-5, "df": 1e-8}
 
 
 @pytest.fixture(scope="module")
@@ -42,6 +42,28 @@ def _gpu_hv(ftk, cl, K, J, prec, vs, tile_bits=0):
     info = ctx.plan_info()
     ctx.close()
     return res, info
+
+
+@pytest.mark.parametrize("n,tile_bits,B", [(2, 0, 1), (8, 0, 1), (12, 6, 1), (12, 0, 2), (16, 0, 1), (18, 0, 4)])
+def test_hv_parity_df(ftk, n, tile_bits, B):
+    """Double-float H.v (hi + lo float pairs in and out) against the oracle:
+    FP64-class accuracy (<= 1e-12 relative)."""
+    import torch
+    cl = named(n)
+    K, J = -1.0, 0.1
+    vs = random_vectors(n, B, 77 + n)
+    hi = vs.astype(np.complex64)
+    lo = (vs - hi.astype(np.complex128)).astype(np.complex64)
+    ctx = ftk.Context(cl, K, J, "df", max_rhs=B, tile_bits=tile_bits)
+    v = torch.from_numpy(np.concatenate([hi, lo])).cuda().contiguous()
+    out = ctx.hv(v)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    got = o[:B].astype(np.complex128) + o[B:].astype(np.complex128)
+    ctx.close()
+    for j in range(B):
+        ref = sparse.hv(cl, K, J, vs[j])
+        assert rel(got[j], ref) <= 1e-12
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -258,7 +280,7 @@ def _pipeline(ftk, prec, eta, tol, qis=(1, 3)):
         for s in range(len(steps)):
             ctx.apply_op(s, 2, q, s)
         G, it, _ = ctx.shifted_cocg(list(range(len(steps))), omega, eta, tol=tol, max_iter=6000,
-                                    allow_noconv=(prec != "fp64"))
+                                    allow_noconv=(prec in ("fp32", "mixed")))
         S, tr = ctx.spectrum(G, T)
         ref = dense.dense_estimator(dg, psi0, ell, n_steps, se, 2, q, omega, eta, T)
         out.append((G, S, tr, ref, it))
@@ -267,12 +289,12 @@ def _pipeline(ftk, prec, eta, tol, qis=(1, 3)):
 
 
 @pytest.mark.parametrize("prec,eta", [("fp64", 0.02), ("fp64", 0.1), ("fp32", 0.1), ("mixed", 0.02),
-                                      ("mixed", 0.1)])
+                                      ("mixed", 0.1), ("df", 0.02)])
 def test_pipeline_vs_dense_estimator(ftk, prec, eta):
     """Whole pipeline against the eigenbasis estimator: <= 1e-8 (FP64),
     <= 1e-5 (FP32 at eta = 0.1; the mixed mode, FP32 H.v with FP64 Krylov
     vectors, also at eta = 0.02) relative, and the same truncation flags."""
-    tol = 1e-11 if prec == "fp64" else 1e-6
+    tol = 1e-11 if prec in ("fp64", "df") else 1e-6
     for G, S, tr, ref, it in _pipeline(ftk, prec, eta, tol):
         assert rel(G.ravel(), ref["G"].ravel()) <= TOL_S[prec]
         assert rel(S, ref["S"]) <= TOL_S[prec]
