@@ -25,7 +25,7 @@ struct Bond { int i, j, g; };
 
 // Workspace regions (bytes from the workspace base).
 struct Layout {
-    size_t psi[2], shells, probes, kry[3], partials, shift, omega, gbuf, tbuf, total;
+    size_t psi[2], shells, probes, kry[3], lam_split, partials, shift, omega, gbuf, tbuf, total;
     size_t vec_bytes;
 };
 
@@ -45,6 +45,9 @@ Layout make_layout(int n, int n_saved, int max_rhs, int prec) {
     L.shells = off; off = align_up(off + vb * n_saved);
     L.probes = off; off = align_up(off + vb * max_rhs);
     for (int i = 0; i < 3; ++i) { L.kry[i] = off; off = align_up(off + vb * max_rhs); }
+    // mixed and double-float modes: the probe vectors split into float hi + lo
+    L.lam_split = off;
+    if (prec == FTK_MIXED || prec == FTK_DF) off = align_up(off + (size_t(1) << n) * 16 * max_rhs);
     L.partials = off; off = align_up(off + kPartialsBytes);
     L.shift = off; off = align_up(off + size_t(kShiftArrays) * max_rhs * FTK_MAX_OMEGA * 16);
     L.omega = off; off = align_up(off + FTK_MAX_OMEGA * 8);
@@ -601,6 +604,7 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     ua.all_done = &d->all_done;
     ua.lo_stride = (long long)ctx->max_rhs * (long long)ctx->dim;   // mixed and double-float modes
     ua.w_lo = ctx->prec == FTK_DF ? ua.lo_stride : 0;
+    ua.lam_split = reinterpret_cast<float4 *>(wsp(ctx, ctx->L.lam_split));
     EpiArgs ea{};
     ea.partials = (double *)wsp(ctx, ctx->L.partials);
     ea.counter = &d->counters[4];

@@ -44,6 +44,24 @@ template <> struct Acc<float> {
         add(p);
         c += e;
     }
+    // adds (ah + al)(bh + bl): the hi x hi product exactly (FMA two-product),
+    // the cross terms in float (their lo x lo term is below the pair precision)
+    __device__ __forceinline__ void fma_pair(float ah, float al, float bh, float bl) {
+        float p = ah * bh;
+        float e = fmaf(ah, bh, -p);
+        e = fmaf(ah, bl, e);
+        e = fmaf(al, bh, e);
+        add(p);
+        c += e;
+    }
+    // adds (ah + al) b
+    __device__ __forceinline__ void fma_hl(float ah, float al, float b) {
+        float p = ah * b;
+        float e = fmaf(ah, b, -p);
+        e = fmaf(al, b, e);
+        add(p);
+        c += e;
+    }
     __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 

@@ -132,11 +132,12 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
     const R scale = (EPI == EPI_TPQ) ? (R)(*ea.scale) : (R)1;
     const R ell = (R)ea.ell, inv_n = (R)ea.inv_n;
     // EPI_COCG_MIXED: the mixed mode's COCG epilogue; its input is the hi part
-    // of a float hi + lo residual and mu is accumulated in double from hi + lo
+    // of a float hi + lo residual and mu is accumulated from hi + lo with
+    // exact FMA two-products and two-sums (double-float, ~48 bits) on the
+    // FP32 pipe
     constexpr bool MIX = EPI == EPI_COCG_MIXED;
     constexpr int ND = (EPI == EPI_TPQ) ? 2 : ((EPI == EPI_COCG || MIX) ? 2 * B : 1);
-    typedef typename std::conditional<MIX, Acc<double>, Acc<R>>::type AccT;
-    AccT dot[ND];
+    Acc<R> dot[ND];
     const bool first = pd.first != 0;
 
     // async copy of a tile of `src` (the thread's own elements) into buf
@@ -263,18 +264,16 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                         dot[2 * j + 1].fma2(pim[k][j], ar[k][j]);
                     }
                 } else if constexpr (MIX) {
-                    // mixed mode: R = hi + lo, mu_j = R_j^T W_j in double
+                    // mixed mode: R = hi + lo, mu_j = R_j^T W_j in double-float
 #pragma unroll
                     for (int j = 0; j < B; ++j) {
                         ok[(size_t)j * ld] = mk<R>(ar[k][j], ai[k][j]);
                         const float2 lo =
                             reinterpret_cast<const float2 *>(ea.lo)[tofs + eofs(k) + (size_t)j * ld];
-                        const double vr = (double)pr[k][j] + (double)lo.x, vi = (double)pim[k][j] + (double)lo.y;
-                        const double wr = ar[k][j], wi = ai[k][j];
-                        dot[2 * j].fma2(vr, wr);
-                        dot[2 * j].fma2(-vi, wi);
-                        dot[2 * j + 1].fma2(vr, wi);
-                        dot[2 * j + 1].fma2(vi, wr);
+                        dot[2 * j].fma_hl(pr[k][j], lo.x, ar[k][j]);
+                        dot[2 * j].fma_hl(-pim[k][j], -lo.y, ai[k][j]);
+                        dot[2 * j + 1].fma_hl(pr[k][j], lo.x, ai[k][j]);
+                        dot[2 * j + 1].fma_hl(pim[k][j], lo.y, ar[k][j]);
                     }
                 }
             }
@@ -409,7 +408,7 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
         dgh[k] = (float)d;
         dgl[k] = (float)(d - (double)dgh[k]);
     }
-    Acc<double> dot[2];
+    Acc<float> dot[2];
     const bool first = pd.first != 0;
     auto issue = [&](const float2 *src, long long tofs, float2 *bh, float2 *bl) {
         if (act) {
@@ -499,13 +498,11 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
                 ok[0] = make_float2(rh, ih);
                 ok[lo] = make_float2(rl, il);
                 if (EPI == EPI_COCG && pd.last) {
-                    // mu = r^T w (bilinear) in double from hi + lo
-                    const double vr = (double)ph[k].x + (double)pl[k].x, vi = (double)ph[k].y + (double)pl[k].y;
-                    const double wr = (double)rh + (double)rl, wi = (double)ih + (double)il;
-                    dot[0].fma2(vr, wr);
-                    dot[0].fma2(-vi, wi);
-                    dot[1].fma2(vr, wi);
-                    dot[1].fma2(vi, wr);
+                    // mu = r^T w (bilinear) in double-float from hi + lo
+                    dot[0].fma_pair(ph[k].x, pl[k].x, rh, rl);
+                    dot[0].fma_pair(-ph[k].y, -pl[k].y, ih, il);
+                    dot[1].fma_pair(ph[k].x, pl[k].x, ih, il);
+                    dot[1].fma_pair(ph[k].y, pl[k].y, rh, rl);
                 }
             }
         }

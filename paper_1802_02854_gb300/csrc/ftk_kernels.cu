@@ -136,11 +136,12 @@ __global__ void __launch_bounds__(256) cocg_update_kernel(V vec, UpdArgs ua) {
 // pairs, lo ua.lo_stride float2 after hi; w is float, or a pair with its lo
 // ua.w_lo float2 after hi in the double-float mode) are updated in double-float
 // arithmetic on the FP32 pipe (about 48 bits, the precision of the stored
-// pairs); of the dots, only the one that decides the recurrence keeps double
-// accuracy: rho = r^T r and g = lambda^dag r sum the exact double products
-// of the hi parts in double and the small hi x lo cross terms in float;
+// pairs). The dots rho = r^T r and g = lambda^dag r accumulate the exact FMA
+// two-products of the hi parts plus the hi x lo cross terms with two-sums
+// (double-float, ~48 bits; the FP64 pipe is not used in the element loop);
 // |r|^2 (the convergence test) uses the hi parts with compensated float
-// accumulation. lambda is stored in double.
+// accumulation. Mode 0 splits the FP64 lambda once into float hi + lo
+// (ua.lam_split), which the iterations read.
 __global__ void __launch_bounds__(256)
 cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, UpdArgs ua) {
     __shared__ double red[(256 / 32) * 5];
@@ -160,20 +161,21 @@ cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, 
         f = (float)s.rescale;   // range guard: a power of two
     }
     const double2 *lam = reinterpret_cast<const double2 *>(ua.lambda[j]);
-    double s_rr = 0, s_ri = 0, s_gr = 0, s_gi = 0;
-    float c_rr = 0, c_ri = 0, c_gr = 0, c_gi = 0;
-    Acc<float> d_n;
+    float4 *lsp = ua.lam_split + off;
+    Acc<float> d_rr, d_ri, d_gr, d_gi, d_n;
     if (!skip) {
         for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
              x += (uint64_t)gridDim.x * blockDim.x) {
-            const double2 ld = lam[x];
-            const float lxr = (float)ld.x, lxi = (float)ld.y;
-            const float lxr_lo = (float)(ld.x - (double)lxr), lxi_lo = (float)(ld.y - (double)lxi);
+            float4 l4;
             dcl r;
             const size_t i = off + x;
             if (ua.mode == 0) {
+                const double2 ld = lam[x];
                 r = {dfl_from(ld.x), dfl_from(ld.y)};
+                l4 = make_float4(r.re.hi, r.im.hi, r.re.lo, r.im.lo);
+                lsp[x] = l4;
             } else {
+                l4 = lsp[x];
                 const float2 ch = rcur[i], cl = rcur[i + lo], ph = rnew[i], pl = rnew[i + lo], wv = w[i];
                 const float2 wl = ua.w_lo ? w[i + ua.w_lo] : make_float2(0.f, 0.f);   // double-float w
                 const dcl rc = {{ch.x, cl.x}, {ch.y, cl.y}};
@@ -191,21 +193,18 @@ cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, 
             }
             rnew[i] = make_float2(r.re.hi, r.im.hi);
             rnew[i + lo] = make_float2(r.re.lo, r.im.lo);
-            const double xh = r.re.hi, yh = r.im.hi;
-            s_rr = fma(xh, xh, fma(-yh, yh, s_rr));
-            s_ri = fma(2.0 * xh, yh, s_ri);
-            c_rr = fmaf(2.f * r.re.hi, r.re.lo, fmaf(-2.f * r.im.hi, r.im.lo, c_rr));
-            c_ri = fmaf(2.f * r.re.hi, r.im.lo, fmaf(2.f * r.re.lo, r.im.hi, c_ri));
-            // g = lambda^dag r: exact hi x hi products in double, cross terms in float
-            const double lx = lxr, ly = lxi;
-            s_gr = fma(lx, xh, fma(ly, yh, s_gr));
-            s_gi = fma(lx, yh, fma(-ly, xh, s_gi));
-            c_gr = fmaf(lxr, r.re.lo, fmaf(lxr_lo, r.re.hi, fmaf(lxi, r.im.lo, fmaf(lxi_lo, r.im.hi, c_gr))));
-            c_gi = fmaf(lxr, r.im.lo, fmaf(lxr_lo, r.im.hi, fmaf(-lxi, r.re.lo, fmaf(-lxi_lo, r.re.hi, c_gi))));
+            // rho = r^T r and g = lambda^dag r in double-float
+            d_rr.fma_pair(r.re.hi, r.re.lo, r.re.hi, r.re.lo);
+            d_rr.fma_pair(-r.im.hi, -r.im.lo, r.im.hi, r.im.lo);
+            d_ri.fma_pair(2.f * r.re.hi, 2.f * r.re.lo, r.im.hi, r.im.lo);
+            d_gr.fma_pair(l4.x, l4.z, r.re.hi, r.re.lo);
+            d_gr.fma_pair(l4.y, l4.w, r.im.hi, r.im.lo);
+            d_gi.fma_pair(l4.x, l4.z, r.im.hi, r.im.lo);
+            d_gi.fma_pair(-l4.y, -l4.w, r.re.hi, r.re.lo);
             d_n.fma2(r.re.hi, r.re.hi); d_n.fma2(r.im.hi, r.im.hi);
         }
     }
-    double v[5] = {s_rr + c_rr, s_ri + c_ri, s_gr + c_gr, s_gi + c_gi, d_n.get()};
+    double v[5] = {d_rr.get(), d_ri.get(), d_gr.get(), d_gi.get(), d_n.get()};
     block_reduce<5>(v, red);
     const unsigned nblk = gridDim.x * gridDim.y;
     double *part = ua.partials + ((size_t)j * gridDim.x + blockIdx.x) * 5;

@@ -30,6 +30,8 @@ struct UpdArgs {
     const int *all_done;
     long long lo_stride;     // mixed / double-float: float2 offset of the lo parts from the hi parts
     long long w_lo;          // double-float mode: float2 offset of w's lo part (0: w is float)
+    float4 *lam_split;       // mixed / double-float: lambda as (hi.re, hi.im, lo.re, lo.im), [B][dim];
+                             // written by mode 0, read by mode 1
 };
 
 struct SeedArgs {
