@@ -5,17 +5,19 @@ Workload (the 24-site FTKomega configuration at scale): periodic honeycomb
 ftk_suggest_order. One step = one pass of the whole hot path over one batch:
   * 21 mTPQ steps (l = 0.5, FP64) from a seeded Philox state, shells k = 0, 20
   * S^z and S^x at momentum Q1 on both shells (4 probes)
-  * one blocked shifted-COCG solve of the 4 probes in the mixed mode (FP32
-    H.V, FP64 Krylov vectors), 1024 shifts on [-3, 3], eta = 0.02, to the
-    paper's residual 1e-4; block plan chosen by ftk_autotune
+  * one blocked shifted-COCG solve of the 4 probes in the double-float mode
+    (H.V and Krylov vectors as float hi + lo pairs on the FP32 pipe, ~48
+    bits), 1024 shifts on [-3, 3], eta = 0.02, to the paper's residual 1e-4;
+    block plan chosen by ftk_autotune (--solve-prec picks another mode)
   * the two spectra (S^z, S^x at Q1) reweighted over the shells to 32
     temperatures in [0.005, 2]
 value = algorithmic H.v bytes of the step (2 * 2^N * s per vector product,
-s = 16 B for the FP64 mTPQ products, 8 B for the FP32 COCG products) / step
-time, in GB/s ("H.v GB/s"). Beside it: spectra/s of this step and of the
-plain FP64 single-vector FTKomega on the same GPU (same seed), the spectrum
-error against that FP64 run, per-step latency p50/p99, and the roofline of
-the dominant kernel (the FP32 H.V of the solve, timed alone).
+s = 16 B for the FP64 mTPQ and the double-float COCG products, 8 B for FP32
+ones) / step time, in GB/s ("H.v GB/s"). Beside it: spectra/s of this step
+and of the plain FP64 single-vector FTKomega on the same GPU (same seed), the
+spectrum error against that FP64 run, per-step latency p50/p99, the roofline
+of the dominant kernel (the double-float H.V of the solve, timed alone: FP32
+pipe bound) and the FP32 H.V against the HBM peak.
 
 --impl reference runs the oracle (plain C/OpenMP FP64, test infrastructure)
 on the host cores on a bounded sample of the same workload.
@@ -44,6 +46,15 @@ N_OMEGA, W_MIN, W_MAX, ETA = 1024, -3.0, 3.0, 0.02
 N_T = 32
 TOL, MAX_ITER = 1e-4, 6000
 METRIC = "H·v GB/s vs HBM peak at N=24; spectra/s at 1e-5 err vs plain FP64; p50/p99"
+SOLVE_BYTES = {"fp64": 16, "df": 16, "mixed": 8, "fp32": 8}   # bytes per amplitude of a COCG H.v
+DTYPE = {"fp64": "f64", "df": "f32x2 (double-float) H.v and Krylov vectors, f64 scalars",
+         "mixed": "f32 H.v, f32x2 Krylov vectors, f64 scalars", "fp32": "f32 H.v, f64 scalars"}
+# FP32-pipe operations of the double-float H.v per amplitude and term (a bond
+# or the diagonal): two real double-float multiply-accumulates of 12
+# operations each (FMA two-product with the cross terms: 4; two-sum and the
+# lo update: 8)
+DF_OPS_PER_TERM = 24
+FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070
 
 
 def peaks():
@@ -149,11 +160,12 @@ def run_step(ctx, cl, omega, temps, seed, sample, slots=None):
     return iters, G, S
 
 
-def time_hv(ctx, torch, n_rhs, dt, reps=10):
+def time_hv(ctx, torch, n_rhs, dt, reps=10, rows=None):
     """Average time of one H.V (all passes) of n_rhs vectors, CUDA events on
-    the context stream; inputs larger than L2."""
+    the context stream; inputs larger than L2. rows: vector rows of the
+    buffer (2 n_rhs for double-float: hi block, lo block)."""
     import paper_1802_02854_gb300 as ftk
-    v = torch.randn(n_rhs, ctx.dim, dtype=dt, device="cuda")
+    v = torch.randn(rows or n_rhs, ctx.dim, dtype=dt, device="cuda")
     out = torch.empty_like(v)
     torch.cuda.synchronize()
     for _ in range(3):
@@ -185,19 +197,21 @@ def run_gpu(args):
     temps = log_temperatures(0.005, 2.0, N_T)
     n_rhs = len(PROBES)
     dim = cl.dim
-    ctx = ftk.Context(cl, K_COUPLING, J_COUPLING, "mixed", max_rhs=n_rhs, n_saved=2)
+    prec = args.solve_prec
+    ctx = ftk.Context(cl, K_COUPLING, J_COUPLING, prec, max_rhs=n_rhs, n_saved=2)
     tuned = {"cocg": ctx.autotune(n_rhs, 0), "tpq": ctx.autotune(1, 1)}   # (tile bits, cols, us)
     stream = ctx.stream
+    es = SOLVE_BYTES[prec]
 
     for w in range(args.warmup):
         run_step(ctx, cl, omega, temps, 100 + w, rank)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    times, iters_tot = [], 0
+    iters_tot = 0
     l0 = ctx.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    S_mixed = None
+    S_fast = None
     with Clocks() as clk:
         torch.cuda.synchronize()
         for s in range(args.steps):
@@ -206,7 +220,7 @@ def run_gpu(args):
             ev[s][1].record(stream)
             iters_tot += int(np.max(it))
             if s == 0:
-                S_mixed = S
+                S_fast = S
         torch.cuda.synchronize()
     launches = ctx.launch_count() - l0
     times = [a.elapsed_time(b) / 1e3 for a, b in ev]
@@ -216,21 +230,42 @@ def run_gpu(args):
         tt = torch.tensor([t_total], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt.item())
-    # algorithmic H.v bytes of the steps: FP64 mTPQ products + FP32 COCG products
-    hv_bytes = args.steps * TPQ_STEPS * 2 * dim * 16 + iters_tot * n_rhs * 2 * dim * 8
+    # algorithmic H.v bytes of the steps: FP64 mTPQ products + COCG products
+    hv_bytes = args.steps * TPQ_STEPS * 2 * dim * 16 + iters_tot * n_rhs * 2 * dim * es
     value = world * hv_bytes / t_total / 1e9
     spectra_per_s = world * args.steps * len(KINDS) / t_total
 
-    # dominant kernel: the FP32 blocked H.V of the solve (autotuned plan), alone
-    t_hv = time_hv(ctx, torch, n_rhs, torch.complex64)
-    n_pass, tile_bits = ctx.plan_info()
+    # dominant kernel: the blocked H.V of the solve (autotuned plan), alone
     peak, peak_kind = peaks()
-    achieved = n_rhs * 2 * dim * 8 / t_hv / 1e9
-    t_hv1 = None
+    n_pass, tile_bits = ctx.plan_info()
+    if prec == "df":
+        t_hv = time_hv(ctx, torch, n_rhs, torch.complex64, rows=2 * n_rhs)
+        ops = n_rhs * dim * (len(cl.bonds) + 1) * DF_OPS_PER_TERM
+        alu_peak = FP32_LANES_PER_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": round(ops / t_hv / 1e12, 3), "peak": round(alu_peak, 2),
+                "unit": "Tops/s (FP32 pipe, an FMA counts once)", "frac": round(ops / t_hv / 1e12 / alu_peak, 4),
+                "traffic": None, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                "kernel": f"hv_pass_df_kernel (double-float H.v, {n_rhs} columns, one per launch; tile "
+                          f"2^{tile_bits}, {n_pass} passes)",
+                "ops_per_launch_set": ops, "hv_us": round(t_hv * 1e6, 2),
+                "hbm": {"gbs": round(n_rhs * 2 * dim * 16 / t_hv / 1e9, 2),
+                        "frac": round(n_rhs * 2 * dim * 16 / t_hv / 1e9 / peak, 4)}}
+    else:
+        dt = torch.complex128 if prec == "fp64" else torch.complex64
+        t_hv = time_hv(ctx, torch, n_rhs, dt)
+        achieved = n_rhs * 2 * dim * es / t_hv / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "kernel": f"hv_pass {prec} B={n_rhs} (one H.v = all passes; tile 2^{tile_bits}, "
+                          f"{tuned['cocg'][1]} columns per launch)", "hv_us": round(t_hv * 1e6, 2)}
+    # the metric's H.v against the HBM peak: FP32, one vector, all passes
     ctx1 = ftk.Context(cl, K_COUPLING, J_COUPLING, "fp32", max_rhs=1)
     t_hv1 = time_hv(ctx1, torch, 1, torch.complex64)
     p1 = ctx1.plan_info()
     ctx1.close()
+    roof["hv_fp32_b1"] = {"us": round(t_hv1 * 1e6, 2), "gbs": round(2 * dim * 8 / t_hv1 / 1e9, 2),
+                          "frac": round(2 * dim * 8 / t_hv1 / 1e9 / peak, 4), "peak": peak,
+                          "peak_kind": peak_kind, "passes": p1[0]}
 
     # plain FP64 single-vector FTKomega on the same GPU, same seed as timed step 0
     ctx64 = ftk.Context(cl, K_COUPLING, J_COUPLING, "fp64", max_rhs=1, n_saved=2)
@@ -240,21 +275,21 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t64 = time.perf_counter() - t0
     ctx64.close()
-    errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(S_mixed, S64)]
+    errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(S_fast, S64)]
     err = max(errs)
 
     # end to end through the public API with host buffers
-    e2e = run_e2e(ctx, cl, omega, temps, args)
+    e2e = run_e2e(ctx, cl, omega, temps, args, es)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * t_total / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 H.v, f64 Krylov vectors/scalars", "data": "synthetic",
-        "config": {"workload": "honeycomb24 FTKw, mixed precision: 3x4 torus, K=-1, J=0.05, dim 2^24; 21 FP64 "
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+        "config": {"workload": f"honeycomb24 FTKw, {prec} solve: 3x4 torus, K=-1, J=0.05, dim 2^24; 21 FP64 "
                                "mTPQ steps (shells k=0,20); S^z and S^x at Q1 on both shells = 4 RHS in one "
-                               "blocked COCG (FP32 H.v, FP64 Krylov vectors); 1024 shifts on [-3,3], eta=0.02, "
+                               f"blocked COCG ({DTYPE[prec]}); 1024 shifts on [-3,3], eta=0.02, "
                                "tol 1e-4; 2 spectra x 32 T in [0.005,2]",
-                   "n_sites": N_SITES, "n_rhs": n_rhs, "n_omega": N_OMEGA, "n_T": N_T,
+                   "n_sites": N_SITES, "n_rhs": n_rhs, "n_omega": N_OMEGA, "n_T": N_T, "solve_precision": prec,
                    "site_order": "ftk_suggest_order", "autotune": tuned,
                    "l2": "inputs larger than L2 (128-256 MiB per vector)", "parallelism": f"replicas{world}"},
         "spectra_per_s": round(spectra_per_s, 4),
@@ -265,13 +300,7 @@ def run_gpu(args):
         "latency_s": {"p50": round(float(np.percentile(times, 50)), 4),
                       "p99": round(float(np.percentile(times, 99)), 4)},
         "krylov_iters_per_step": iters_tot / args.steps,
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": f"hv_pass fp32 B={n_rhs} (one H.v = all passes; tile 2^{tuned['cocg'][0]}, "
-                               f"{tuned['cocg'][1]} columns per launch)",
-                     "peak_kind": peak_kind, "hv_us": round(t_hv * 1e6, 2),
-                     "hv_fp32_b1": {"us": round(t_hv1 * 1e6, 2), "gbs": round(2 * dim * 8 / t_hv1 / 1e9, 2),
-                                    "frac": round(2 * dim * 8 / t_hv1 / 1e9 / peak, 4), "passes": p1[0]}},
+        "roofline": roof,
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -286,7 +315,7 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_e2e(ctx, cl, omega, temps, args):
+def run_e2e(ctx, cl, omega, temps, args, es):
     """The same step through the public API with host buffers: the initial
     state is copied in from pinned host memory, G and the spectra come back
     to the host (inside the timed region)."""
@@ -298,7 +327,7 @@ def run_e2e(ctx, cl, omega, temps, args):
     host = pinned.numpy().view(np.complex128)
     n_rhs = len(PROBES)
     torch.cuda.synchronize()
-    n = max(1, min(args.steps, 2))
+    n = 1
     t0 = time.perf_counter()
     hv_bytes = 0
     for s in range(n):
@@ -310,7 +339,7 @@ def run_e2e(ctx, cl, omega, temps, args):
                                      allow_noconv=True)
         for p in range(len(KINDS)):
             ctx.spectrum(np.stack([G[2 * p], G[2 * p + 1]]), temps)
-        hv_bytes += TPQ_STEPS * 2 * cl.dim * 16 + int(np.max(it)) * n_rhs * 2 * cl.dim * 8
+        hv_bytes += TPQ_STEPS * 2 * cl.dim * 16 + int(np.max(it)) * n_rhs * 2 * cl.dim * es
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return {"value": round(hv_bytes / dt / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": int(cl.dim * 16),
@@ -377,7 +406,7 @@ def run_hv_only(args):
     if args.hv_autotune:
         ctx.autotune(args.hv_rhs, 0)
     dt = torch.complex128 if prec == "fp64" else torch.complex64
-    v = torch.randn(args.hv_rhs, cl.dim, dtype=dt, device="cuda")
+    v = torch.randn(args.hv_rhs * (2 if prec == "df" else 1), cl.dim, dtype=dt, device="cuda")
     out = torch.empty_like(v)
     torch.cuda.synchronize()
     for _ in range(args.hv_reps):
@@ -398,11 +427,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hv-only", action="store_true", help="only a few H.V launches (profiling)")
     ap.add_argument("--hv-sites", type=int, default=N_SITES)
-    ap.add_argument("--hv-prec", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--hv-prec", default="fp32", choices=["fp64", "fp32", "df"])
     ap.add_argument("--hv-rhs", type=int, default=4)
     ap.add_argument("--hv-reps", type=int, default=4)
     ap.add_argument("--hv-autotune", action="store_true")
     ap.add_argument("--max-iter", type=int, default=0, help="cap Krylov iterations (profiling runs)")
+    ap.add_argument("--solve-prec", default="df", choices=["df", "mixed", "fp64", "fp32"],
+                    help="precision mode of the blocked COCG solve")
     args = ap.parse_args()
     global MAX_ITER
     if args.max_iter > 0:
