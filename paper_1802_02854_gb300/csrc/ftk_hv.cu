@@ -116,18 +116,29 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
             if ((tau >> q) & 1) v |= 1ull << pd.free_pos[q];
         return (long long)v;
     };
-    // diagonal of this pass's bonds at the thread's offsets:
-    // +dg (parallel) / -dg (antiparallel), parity = thread part ^ register part
+    // diagonal of this pass's bonds at the thread's offsets: dgv[0] c0 +
+    // dgv[1] c1 with integer counts c (+1 parallel, -1 antiparallel; parity
+    // = thread part ^ register part), two multiply-adds per amplitude
     R dg[E];
+    {
+        int c0[E], c1[E];
 #pragma unroll
-    for (int k = 0; k < E; ++k) dg[k] = (R)0;
-    for (int l = 0; l < pd.n_bonds; ++l) {
-        const int m = (1 << pd.bi[l]) | (1 << pd.bj[l]);
-        const int pt = __popc(t & m & (T - 1)) & 1;
-        const int km = m >> tb;
-        const R d = Coef<R>::dgv(pd, pd.dgc[l]);
+        for (int k = 0; k < E; ++k) { c0[k] = 0; c1[k] = 0; }
+        for (int l = 0; l < pd.n_bonds; ++l) {
+            const int m = (1 << pd.bi[l]) | (1 << pd.bj[l]);
+            const int pt = __popc(t & m & (T - 1)) & 1;
+            const int km = m >> tb;
+            const int cls = pd.dgc[l];
 #pragma unroll
-        for (int k = 0; k < E; ++k) dg[k] += ((pt ^ __popc(k & km)) & 1) ? -d : d;
+            for (int k = 0; k < E; ++k) {
+                const int sg = 1 - 2 * ((pt ^ __popc(k & km)) & 1);
+                c0[k] += cls ? 0 : sg;
+                c1[k] += cls ? sg : 0;
+            }
+        }
+        const R d0 = Coef<R>::dgv(pd, 0), d1 = Coef<R>::dgv(pd, 1);
+#pragma unroll
+        for (int k = 0; k < E; ++k) dg[k] = (R)c0[k] * d0 + (R)c1[k] * d1;
     }
     const R scale = (EPI == EPI_TPQ) ? (R)(*ea.scale) : (R)1;
     const R ell = (R)ea.ell, inv_n = (R)ea.inv_n;
@@ -394,19 +405,32 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
             if ((tau >> q) & 1) v |= 1ull << pd.free_pos[q];
         return (long long)v;
     };
-    // diagonal (double, split once per thread)
+    // diagonal dgv[0] c0 + dgv[1] c1 (integer counts c as in the kernel
+    // above) in double-float arithmetic, once per thread
     float dgh[E], dgl[E];
+    {
+        int c0[E], c1[E];
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-        double d = 0.0;
+        for (int k = 0; k < E; ++k) { c0[k] = 0; c1[k] = 0; }
         for (int l = 0; l < pd.n_bonds; ++l) {
             const int m = (1 << pd.bi[l]) | (1 << pd.bj[l]);
             const int pt = __popc(t & m & (T - 1)) & 1;
-            const double c = pd.dgv[pd.dgc[l]];
-            d += ((pt ^ __popc(k & (m >> tb))) & 1) ? -c : c;
+            const int km = m >> tb;
+            const int cls = pd.dgc[l];
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const int sg = 1 - 2 * ((pt ^ __popc(k & km)) & 1);
+                c0[k] += cls ? 0 : sg;
+                c1[k] += cls ? sg : 0;
+            }
         }
-        dgh[k] = (float)d;
-        dgl[k] = (float)(d - (double)dgh[k]);
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const dfl d = dfl_add(dfl_mul({(float)c0[k], 0.f}, {pd.dgv_f[0], pd.dgv_lo[0]}),
+                                  dfl_mul({(float)c1[k], 0.f}, {pd.dgv_f[1], pd.dgv_lo[1]}));
+            dgh[k] = d.hi;
+            dgl[k] = d.lo;
+        }
     }
     Acc<float> dot[2];
     const bool first = pd.first != 0;
