@@ -519,6 +519,20 @@ static int upd_kind(const ftk_ctx *ctx) { return ctx->prec >= FTK_MIXED ? 2 : ct
 static ftk_status cocg_iteration(ftk_ctx *ctx, int B, void *rcur, void *rprev, void *w,
                                  EpiArgs ea, const SeedArgs &sa, const ShiftArgs &sh,
                                  UpdArgs ua) {
+    if (ctx->prec == FTK_DF) {
+        // double-float: the update r_{k-1} <- r_{k+1} of the previous step runs
+        // inside the first pass of H r_{k+1} (rcur = r_k, rprev = r_{k-1})
+        ea.df_lo = ua.lo_stride;
+        ea.fu_seed = ua.seed;
+        ea.fu_rcur = static_cast<float2 *>(rcur);
+        ea.fu_lam = ua.lam_split;
+        ea.fu_result = ua.result;
+        ftk_status s = run_hv(ctx, ctx->mprec, B, EPI_COCG, rprev, w, ea);
+        if (s) return s;
+        LAUNCH(launch_cocg_seed(sa, ctx->stream));
+        LAUNCH(launch_cocg_shift(sh, B, ctx->stream));
+        return FTK_OK;
+    }
     if (ctx->prec == FTK_MIXED) ea.lo = static_cast<const char *>(rcur) + size_t(8) * ua.lo_stride;
     if (ctx->prec == FTK_DF) ea.df_lo = ua.lo_stride;   // r and w: lo arrays one region half later
     ftk_status s = run_hv(ctx, ctx->mprec, B, EPI_COCG, rcur, w, ea);
@@ -638,6 +652,16 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     }
     ua.mode = 0;
     LAUNCH(launch_cocg_update(upd_kind(ctx), B, nullptr, nullptr, rcur, ua, vec_grid(ctx, ctx->dim), ctx->stream));
+    int it0 = 0;
+    if (ctx->prec == FTK_DF) {
+        // step 0 without the fused update: W = H r_0 (+mu), seed, shifts
+        EpiArgs e0 = ea;
+        e0.df_lo = ua.lo_stride;
+        if ((s = run_hv(ctx, ctx->mprec, B, EPI_COCG, rcur, w, e0))) return s;
+        LAUNCH(launch_cocg_seed(sa, ctx->stream));
+        LAUNCH(launch_cocg_shift(sh, B, ctx->stream));
+        it0 = 1;
+    }
 
     // Capture two iterations (buffer roles return to the start) in a graph.
     cudaGraph_t graph = nullptr;
@@ -654,7 +678,7 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     CK(ce);
-    int done = 0, it = 0;
+    int done = 0, it = it0;
     const int chunk = 16;   // graph launches between host checks (32 iterations)
     ftk_status result = FTK_OK;
     while (!done) {

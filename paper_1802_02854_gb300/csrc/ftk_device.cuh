@@ -179,4 +179,47 @@ __host__ __device__ __forceinline__ dcl dcl_mul(dcl a, dcl b) {
     return {dfl_sub(dfl_mul(a.re, b.re), dfl_mul(a.im, b.im)), dfl_add(dfl_mul(a.re, b.im), dfl_mul(a.im, b.re))};
 }
 
+// ------------------------------------------------ COCG residual, split form
+// The scalars of one COCG step for one right-hand side as double-float
+// pairs: seed shift z_s, alpha_k, c_k, and the range-guard factor f (a power
+// of two, 1 when unused).
+struct DfStep {
+    dcl zs, al, cc;
+    float f;
+};
+__device__ __forceinline__ DfStep df_step(const CocgSeed &s) {
+    return {{dfl_from(s.zs_re), dfl_from(s.zs_im)}, {dfl_from(s.alpha_re), dfl_from(s.alpha_im)},
+            {dfl_from(s.c_re), dfl_from(s.c_im)}, (float)s.rescale};
+}
+// Three-term COCG residual (Sec. IV): A r_k = z_s r_k - w_k with w_k = H r_k,
+// r_{k+1} = r_k + c_k (r_k - r_{k-1}) - alpha_k A r_k, scaled by f.
+__device__ __forceinline__ dcl df_next_residual(const dcl &rc, const dcl &rp, const dcl &w, const DfStep &q) {
+    dcl ar = dcl_mul(q.zs, rc);
+    ar.re = dfl_sub(ar.re, w.re);
+    ar.im = dfl_sub(ar.im, w.im);
+    dcl r = dcl_add(rc, dcl_sub(dcl_mul(q.cc, dcl_sub(rc, rp)), dcl_mul(q.al, ar)));
+    if (q.f != 1.f) r = {{r.re.hi * q.f, r.re.lo * q.f}, {r.im.hi * q.f, r.im.lo * q.f}};
+    return r;
+}
+// Per-thread sums of rho = r^T r, g = lambda^dag r (double-float: exact
+// two-products of the hi parts plus cross terms, two-sums) and |r|^2
+// (compensated float of the hi parts). l4 = (lambda hi.re, hi.im, lo.re, lo.im).
+struct DfUpdDots {
+    Acc<float> rr, ri, gr, gi, n;
+    __device__ __forceinline__ void add(const dcl &r, const float4 &l4) {
+        rr.fma_pair(r.re.hi, r.re.lo, r.re.hi, r.re.lo);
+        rr.fma_pair(-r.im.hi, -r.im.lo, r.im.hi, r.im.lo);
+        ri.fma_pair(2.f * r.re.hi, 2.f * r.re.lo, r.im.hi, r.im.lo);
+        gr.fma_pair(l4.x, l4.z, r.re.hi, r.re.lo);
+        gr.fma_pair(l4.y, l4.w, r.im.hi, r.im.lo);
+        gi.fma_pair(l4.x, l4.z, r.im.hi, r.im.lo);
+        gi.fma_pair(-l4.y, -l4.w, r.re.hi, r.re.lo);
+        n.fma2(r.re.hi, r.re.hi);
+        n.fma2(r.im.hi, r.im.hi);
+    }
+    __device__ __forceinline__ void get(double (&v)[5]) const {
+        v[0] = rr.get(); v[1] = ri.get(); v[2] = gr.get(); v[3] = gi.get(); v[4] = n.get();
+    }
+};
+
 }  // namespace ftk

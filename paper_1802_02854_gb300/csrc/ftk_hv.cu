@@ -32,6 +32,8 @@
 namespace ftk {
 
 // ------------------------------------------------------------ async copies
+// L2 prefetch of the 128-byte line holding p (no register result)
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 __device__ __forceinline__ void cp_async_elem(float2 *dst, const float2 *src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
@@ -369,7 +371,7 @@ __device__ __forceinline__ void bond_apply_df(float (&arh)[1 << LE], float (&arl
             bond_apply_df<LE, KA, KB>(arh, arl, aih, ail, ph, pl, csh, csl, cfh, cfl);               \
         break;
 
-template <int LE, int EPI>
+template <int LE, int EPI, bool FU>
 __global__ void __launch_bounds__(512, 1)
 hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd, const EpiArgs ea) {
     constexpr int E = 1 << LE;
@@ -434,6 +436,11 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
     }
     Acc<float> dot[2];
     const bool first = pd.first != 0;
+    // fused residual update (first pass only): a frozen column keeps its
+    // stale residual and produces zero dots
+    DfUpdDots udots;
+    bool fdone = false;
+    if constexpr (FU) fdone = ea.fu_seed->done != 0;
     auto issue = [&](const float2 *src, long long tofs, float2 *bh, float2 *bl) {
         if (act) {
             const float2 *g = src + tofs;
@@ -450,7 +457,7 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
     long tau = blockIdx.x;
     long long tofs = tau < n_tiles ? tile_ofs(tau) : 0;
     if (tau < n_tiles) {
-        issue(in, tofs, bh0, bl0);
+        if (!FU) issue(in, tofs, bh0, bl0);
         if (!first) issue(out, tofs, pbh, pbl);
     }
     for (int it = 0; tau < n_tiles; tau += gridDim.x, ++it) {
@@ -459,10 +466,79 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
         const long tn = tau + gridDim.x;
         const bool more = tn < n_tiles;
         const long long tofs_n = more ? tile_ofs(tn) : 0;
-        if (more) issue(in, tofs_n, nh, nl);
+        if (!FU && more) issue(in, tofs_n, nh, nl);
         if (first) { if (more) cp_async_wait<1>(); else cp_async_wait<0>(); }
         else { if (more) cp_async_wait<2>(); else cp_async_wait<1>(); }
         __syncthreads();
+        if constexpr (FU) {
+            // the tile of r_{k+1}: computed from r_k, r_{k-1}, w_k (all at the
+            // tile's own offsets, read before this thread overwrites them),
+            // written to r_{k+1}'s buffer and to the current shared buffers
+            if (act) {
+                float2 *sh = const_cast<float2 *>(ch), *sl = const_cast<float2 *>(cl);
+                float2 *rn = ea.fu_rnew + tofs, *rc = ea.fu_rcur + tofs, *wk = out + tofs;
+                const float4 *lm = ea.fu_lam + tofs;
+                if (!fdone) {
+                    const DfStep qs = df_step(*ea.fu_seed);
+                    // loads of KB elements first (independent, in flight
+                    // together), then their arithmetic and stores
+                    constexpr int KB = E < 2 ? E : 2;
+#pragma unroll
+                    for (int k0 = 0; k0 < E; k0 += KB) {
+                        float2 ah[KB], al[KB], ph2[KB], pl2[KB], wh[KB], wl[KB];
+                        float4 l4[KB];
+#pragma unroll
+                        for (int u = 0; u < KB; ++u) {
+                            const long long e = eofs(k0 + u);
+                            ah[u] = rc[e]; al[u] = rc[e + lo]; ph2[u] = rn[e]; pl2[u] = rn[e + lo];
+                            wh[u] = wk[e]; wl[u] = wk[e + lo]; l4[u] = lm[e];
+                        }
+#pragma unroll
+                        for (int u = 0; u < KB; ++u) {
+                            const int k = k0 + u;
+                            const long long e = eofs(k);
+                            const dcl r = df_next_residual({{ah[u].x, al[u].x}, {ah[u].y, al[u].y}},
+                                                           {{ph2[u].x, pl2[u].x}, {ph2[u].y, pl2[u].y}},
+                                                           {{wh[u].x, wl[u].x}, {wh[u].y, wl[u].y}}, qs);
+                            if (qs.f != 1.f) {
+                                rc[e] = make_float2(ah[u].x * qs.f, ah[u].y * qs.f);
+                                rc[e + lo] = make_float2(al[u].x * qs.f, al[u].y * qs.f);
+                            }
+                            const float2 nh2 = make_float2(r.re.hi, r.im.hi), nl2 = make_float2(r.re.lo, r.im.lo);
+                            rn[e] = nh2;
+                            rn[e + lo] = nl2;
+                            sh[t + T * k] = nh2;
+                            sl[t + T * k] = nl2;
+                            udots.add(r, l4[u]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < E; ++k) {
+                        const long long e = eofs(k);
+                        sh[t + T * k] = rn[e];
+                        sl[t + T * k] = rn[e + lo];
+                    }
+                }
+            }
+            __syncthreads();
+            // the next tile's update inputs to L2 while this tile's bonds run
+            // (one prefetch per 128-byte line: every 16th lane for float2
+            // arrays, every 8th for the float4 lambda)
+            if (act && more && !fdone) {
+                const int lane = t & 31;
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const long long e = tofs_n + eofs(k);
+                    if ((lane & 15) == 0) {
+                        prefetch_l2(ea.fu_rcur + e); prefetch_l2(ea.fu_rcur + e + lo);
+                        prefetch_l2(ea.fu_rnew + e); prefetch_l2(ea.fu_rnew + e + lo);
+                        prefetch_l2(out + e); prefetch_l2(out + e + lo);
+                    }
+                    if ((lane & 7) == 0) prefetch_l2(ea.fu_lam + e);
+                }
+            }
+        }
         if (act) {
             float arh[E], arl[E], aih[E], ail[E];
             float2 ph[E], pl[E];
@@ -535,6 +611,20 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
         __syncthreads();
     }
     cp_async_wait<0>();
+    if constexpr (FU) {
+        // update dots of r_{k+1} (and mu when this pass is also the last)
+        double v[7];
+        udots.get(*reinterpret_cast<double(*)[5]>(v));
+        v[5] = (EPI == EPI_COCG) ? dot[0].get() : 0.0;
+        v[6] = (EPI == EPI_COCG) ? dot[1].get() : 0.0;
+        block_reduce<7>(v, red);
+        if (threadIdx.x < 7) ea.partials[(size_t)blockIdx.x * 7 + threadIdx.x] = red[threadIdx.x];
+        __shared__ double fin[7];
+        if (!last_block_reduce<7>(ea.partials, ea.counter, fin, red)) return;
+        if (threadIdx.x < 5) ea.fu_result[threadIdx.x] = fin[threadIdx.x];
+        if (EPI == EPI_COCG && pd.last && threadIdx.x < 2) ea.result[threadIdx.x] = fin[5 + threadIdx.x];
+        return;
+    }
     if (EPI != EPI_COCG || !pd.last) return;
     double v[2] = {dot[0].get(), dot[1].get()};
     block_reduce<2>(v, red);
@@ -578,7 +668,7 @@ int hv_threads(const PassDesc &pd) {
 size_t hv_smem_bytes(int prec, int B, const PassDesc &pd) {
     const int bc = std::min(B, hv_max_b(prec));
     const size_t es = prec == 1 ? 8 : 16;
-    const int nd = std::max(2, 2 * bc);
+    const int nd = prec == 2 ? 8 : std::max(2, 2 * bc);   // double-float: fused update dots + mu
     return size_t(3) * ((size_t)1 << pd.tile_bits) * bc * es + (size_t)(hv_threads(pd) / 32) * nd * 8;
 }
 
@@ -714,8 +804,10 @@ static cudaError_t attrs_b() {
 // from several host threads, as the server does).
 template <int LE>
 static cudaError_t attrs_df() {
-    cudaError_t e = opt_in(hv_pass_df_kernel<LE, EPI_PLAIN>);
-    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_COCG>);
+    cudaError_t e = opt_in(hv_pass_df_kernel<LE, EPI_PLAIN, false>);
+    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_COCG, false>);
+    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_PLAIN, true>);
+    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_COCG, true>);
     return e;
 }
 
@@ -805,8 +897,10 @@ static cudaError_t launch_chunk(int bc, int epi, const void *in, void *out, long
 template <int LE>
 static cudaError_t launch_df_le(int epi, const void *in, void *out, const PassDesc &pd, const EpiArgs &ea,
                                 int grid_cap, cudaStream_t st) {
+    const bool fu = ea.fu_seed != nullptr && pd.first;
     void (*k)(const float2 *, float2 *, const PassDesc, const EpiArgs) =
-        epi == EPI_COCG ? hv_pass_df_kernel<LE, EPI_COCG> : hv_pass_df_kernel<LE, EPI_PLAIN>;
+        epi == EPI_COCG ? (fu ? hv_pass_df_kernel<LE, EPI_COCG, true> : hv_pass_df_kernel<LE, EPI_COCG, false>)
+                        : (fu ? hv_pass_df_kernel<LE, EPI_PLAIN, true> : hv_pass_df_kernel<LE, EPI_PLAIN, false>);
     const int threads = hv_threads(pd);
     const size_t smem = hv_smem_bytes(2, 1, pd);
     int per_sm = 0, dev = 0, n_sm = 0;
@@ -830,6 +924,13 @@ static cudaError_t launch_hv_pass_df(int B, int epi, const void *in, void *out, 
     for (int j = 0; j < B; ++j) {
         EpiArgs e = ea;
         if (e.result) e.result += 2 * j;
+        if (e.fu_seed) {   // fused residual update: this column's vectors, seed and dots
+            e.fu_seed += j;
+            e.fu_rcur += (size_t)j * ld;
+            e.fu_rnew = static_cast<float2 *>(const_cast<void *>(in)) + (size_t)j * ld;
+            e.fu_lam += (size_t)j * ld;
+            e.fu_result += (size_t)FTK_UPD_DOTS * j;
+        }
         const void *i = static_cast<const float2 *>(in) + (size_t)j * ld;
         void *o = static_cast<float2 *>(out) + (size_t)j * ld;
         const cudaError_t r = pd.le == 3 ? launch_df_le<3>(epi, i, o, pd, e, grid_cap, st)

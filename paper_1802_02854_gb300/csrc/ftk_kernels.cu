@@ -151,18 +151,11 @@ cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, 
     const size_t off = (size_t)j * n;
     const long long lo = ua.lo_stride;
     const bool skip = ua.mode == 1 && ua.seed[j].done != 0;
-    dcl zs{}, al{}, cc{};
-    float f = 1.f;
-    if (ua.mode == 1) {
-        const CocgSeed &s = ua.seed[j];
-        zs = {dfl_from(s.zs_re), dfl_from(s.zs_im)};
-        al = {dfl_from(s.alpha_re), dfl_from(s.alpha_im)};
-        cc = {dfl_from(s.c_re), dfl_from(s.c_im)};
-        f = (float)s.rescale;   // range guard: a power of two
-    }
+    DfStep q{};
+    if (ua.mode == 1) q = df_step(ua.seed[j]);   // range guard: q.f is a power of two
     const double2 *lam = reinterpret_cast<const double2 *>(ua.lambda[j]);
     float4 *lsp = ua.lam_split + off;
-    Acc<float> d_rr, d_ri, d_gr, d_gi, d_n;
+    DfUpdDots dots;
     if (!skip) {
         for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
              x += (uint64_t)gridDim.x * blockDim.x) {
@@ -178,37 +171,25 @@ cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, 
                 l4 = lsp[x];
                 const float2 ch = rcur[i], cl = rcur[i + lo], ph = rnew[i], pl = rnew[i + lo], wv = w[i];
                 const float2 wl = ua.w_lo ? w[i + ua.w_lo] : make_float2(0.f, 0.f);   // double-float w
-                const dcl rc = {{ch.x, cl.x}, {ch.y, cl.y}};
-                const dcl rp = {{ph.x, pl.x}, {ph.y, pl.y}};
-                // A r = z_s r - w;  r_new = r + c (r - r_prev) - alpha A r
-                dcl ar = dcl_mul(zs, rc);
-                ar.re = dfl_sub(ar.re, {wv.x, wl.x});
-                ar.im = dfl_sub(ar.im, {wv.y, wl.y});
-                r = dcl_add(rc, dcl_sub(dcl_mul(cc, dcl_sub(rc, rp)), dcl_mul(al, ar)));
-                if (f != 1.f) {
-                    r = {{r.re.hi * f, r.re.lo * f}, {r.im.hi * f, r.im.lo * f}};
-                    rcur[i] = make_float2(ch.x * f, ch.y * f);
-                    rcur[i + lo] = make_float2(cl.x * f, cl.y * f);
+                r = df_next_residual({{ch.x, cl.x}, {ch.y, cl.y}}, {{ph.x, pl.x}, {ph.y, pl.y}},
+                                     {{wv.x, wl.x}, {wv.y, wl.y}}, q);
+                if (q.f != 1.f) {
+                    rcur[i] = make_float2(ch.x * q.f, ch.y * q.f);
+                    rcur[i + lo] = make_float2(cl.x * q.f, cl.y * q.f);
                 }
             }
             rnew[i] = make_float2(r.re.hi, r.im.hi);
             rnew[i + lo] = make_float2(r.re.lo, r.im.lo);
-            // rho = r^T r and g = lambda^dag r in double-float
-            d_rr.fma_pair(r.re.hi, r.re.lo, r.re.hi, r.re.lo);
-            d_rr.fma_pair(-r.im.hi, -r.im.lo, r.im.hi, r.im.lo);
-            d_ri.fma_pair(2.f * r.re.hi, 2.f * r.re.lo, r.im.hi, r.im.lo);
-            d_gr.fma_pair(l4.x, l4.z, r.re.hi, r.re.lo);
-            d_gr.fma_pair(l4.y, l4.w, r.im.hi, r.im.lo);
-            d_gi.fma_pair(l4.x, l4.z, r.im.hi, r.im.lo);
-            d_gi.fma_pair(-l4.y, -l4.w, r.re.hi, r.re.lo);
-            d_n.fma2(r.re.hi, r.re.hi); d_n.fma2(r.im.hi, r.im.hi);
+            dots.add(r, l4);
         }
     }
-    double v[5] = {d_rr.get(), d_ri.get(), d_gr.get(), d_gi.get(), d_n.get()};
+    double v[5];
+    dots.get(v);
     block_reduce<5>(v, red);
     const unsigned nblk = gridDim.x * gridDim.y;
     double *part = ua.partials + ((size_t)j * gridDim.x + blockIdx.x) * 5;
     if (threadIdx.x < 5) part[threadIdx.x] = red[threadIdx.x];
+    // last block: fixed-order sum of the partials -> ua.result[B][FTK_UPD_DOTS]
     __shared__ int am_last;
     __threadfence();
     __syncthreads();
@@ -217,11 +198,11 @@ cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, 
     if (!am_last) return;
     __threadfence();
     for (int q = threadIdx.x; q < (int)gridDim.y * 5; q += blockDim.x) {
-        const int jj = q / 5, dd = q % 5;
+        const int jj = q / 5, d = q % 5;
         double sum = 0.0;
         for (unsigned bb = 0; bb < gridDim.x; ++bb)
-            sum += __ldcg(ua.partials + ((size_t)jj * gridDim.x + bb) * 5 + dd);
-        ua.result[jj * FTK_UPD_DOTS + dd] = sum;
+            sum += __ldcg(ua.partials + ((size_t)jj * gridDim.x + bb) * 5 + d);
+        ua.result[jj * FTK_UPD_DOTS + d] = sum;
     }
     if (threadIdx.x == 0) *ua.counter = 0u;
 }

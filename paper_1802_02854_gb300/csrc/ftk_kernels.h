@@ -17,6 +17,17 @@ struct EpiArgs {
     const int *all_done;     // COCG: skip when every RHS finished (or NULL)
     const void *lo;          // COCG, mixed mode: float2 low parts of the input (mu from hi + lo)
     long long df_lo;         // double-float mode: float2 offset of the lo arrays of in and out
+    // Double-float mode, first pass of H r_{k+1}: the COCG residual update
+    // fused in (fu_seed != NULL). Per launch (one column): the pass's input
+    // r_{k+1} is computed tile by tile from r_k (fu_rcur), r_{k-1} (in place
+    // of which r_{k+1} is written: fu_rnew, the pass's `in`), w_k = H r_k (the
+    // pass's `out`, read before it is overwritten) and lambda split
+    // (fu_lam); rho, g, |r|^2 of r_{k+1} go to fu_result[0..5).
+    const CocgSeed *fu_seed;
+    float2 *fu_rcur;
+    float2 *fu_rnew;
+    const float4 *fu_lam;
+    double *fu_result;
 };
 
 struct UpdArgs {
