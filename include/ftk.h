@@ -203,6 +203,18 @@ ftk_status ftk_plan_info(const ftk_ctx *ctx, int32_t *n_passes, int32_t *tile_bi
 ftk_status ftk_suggest_order(int32_t n_sites, const ftk_bond *bonds, int32_t n_bonds, int32_t precision,
                              int32_t n_rhs, int32_t tile_bits, int32_t *perm_out, int32_t *n_passes_out);
 
+/* Relaxed double-float solve (context precision FTK_DF only). theta > 0:
+ * once every unfinished right-hand side of a ftk_shifted_cocg call has a
+ * residual max_s ||r_k|| / |pi^s_k| / ||lambda|| below theta, its remaining
+ * matrix-vector products run in FP32 (3-pass FP32 H.V of the hi parts, mu
+ * from hi + lo) while the residual recurrence, the dots and the shift
+ * recurrences stay double-float / FP64. The product error then enters the
+ * shifted residuals scaled by that small residual (inexact Krylov
+ * relaxation; the measured spectrum error is stated with the bench). theta =
+ * 0 (the default) keeps every product double-float. Returns FTK_EINVAL for a
+ * negative or non-finite theta, or theta > 0 on another precision. */
+ftk_status ftk_set_relax(ftk_ctx *ctx, double theta);
+
 /* Autotuner of the blocked H.V (the batching knob of the Sec. IV.A product
  * on this hardware). Times, on scratch vectors in the context's Krylov
  * region, every admissible plan for n_rhs right-hand sides: column chunk

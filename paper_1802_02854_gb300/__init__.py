@@ -29,7 +29,7 @@ STATUS_NAMES = ["FTK_OK", "FTK_EINVAL", "FTK_ENOMEM", "FTK_ECUDA", "FTK_ENOCONV"
 EXPORTS = ["ftk_footprint", "ftk_create", "ftk_bind_workspace", "ftk_tpq_init", "ftk_set_state",
            "ftk_tpq_step", "ftk_shells", "ftk_apply_op", "ftk_set_probe", "ftk_shifted_cocg",
            "ftk_spectrum", "ftk_hv", "ftk_get_vector", "ftk_plan_info", "ftk_launch_count",
-           "ftk_last_error", "ftk_destroy", "ftk_tpq_step_noalloc", "ftk_suggest_order", "ftk_autotune"]
+           "ftk_last_error", "ftk_destroy", "ftk_tpq_step_noalloc", "ftk_suggest_order", "ftk_autotune", "ftk_set_relax"]
 
 
 class FtkError(RuntimeError):
@@ -90,6 +90,7 @@ def lib() -> C.CDLL:
     L.ftk_tpq_step_noalloc.argtypes = [i32, C.POINTER(_Bond), i32, dbl, dbl, dbl, vp, vp, pd, vp]
     L.ftk_suggest_order.argtypes = [i32, C.POINTER(_Bond), i32, i32, i32, i32, pi, pi]
     L.ftk_autotune.argtypes = [vp, i32, i32, pi, pi, pd]
+    L.ftk_set_relax.argtypes = [vp, C.c_double]
     for name in EXPORTS:
         if name not in ("ftk_footprint", "ftk_launch_count", "ftk_last_error", "ftk_destroy"):
             getattr(L, name).restype = C.c_int
@@ -249,6 +250,11 @@ def ftk_autotune(ctx, n_rhs, which=0):
     return tb.value, cols.value, us.value
 
 
+def ftk_set_relax(ctx, theta):
+    """Relaxed double-float solve threshold theta (0: off); FTK_DF contexts."""
+    _check(ctx, lib().ftk_set_relax(ctx, float(theta)))
+
+
 def ftk_suggest_order(n_sites, bonds, precision=FTK_FP64, n_rhs=1, tile_bits=0):
     """Site relabelling for fewer H.v passes: returns (perm, n_passes) with
     site l -> new label perm[l] (apply with ftk_inputs.relabel)."""
@@ -336,6 +342,9 @@ class Context:
 
     def autotune(self, n_rhs=1, which=0):
         return ftk_autotune(self.handle, n_rhs, which)
+
+    def set_relax(self, theta):
+        ftk_set_relax(self.handle, theta)
 
     def plan_info(self):
         return ftk_plan_info(self.handle)

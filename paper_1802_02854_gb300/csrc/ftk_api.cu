@@ -66,7 +66,7 @@ struct Small {
     double op_dots[4];
     double inv_pi_max[2 * FTK_MAX_RHS];
     int all_done;
-    int pad;
+    int lowp;                        // relaxed solve: FP32 products from here on
     CocgSeed seed[FTK_MAX_RHS];
 };
 
@@ -85,6 +85,7 @@ void set_thread_error(const char *msg);
 struct ftk_ctx {
     int n = 0, nb = 0, prec = 0, max_rhs = 1, n_saved_cap = 1, tile_bits_req = 0;
     int vprec = 0, mprec = 0;   // vector storage / H.v arithmetic: 0 FP64, 1 FP32
+    double relax = 0.0;         // relaxed double-float solve: theta (0: off)
     uint64_t dim = 0;
     double K = 0, J = 0, ell_min = 0;
     std::vector<Bond> bonds;
@@ -162,8 +163,10 @@ bool plan_passes(ftk_ctx *ctx, int prec, int bc, int tile_bits, Plan &pl) {
 ftk_status get_plan(ftk_ctx *ctx, int prec, int B, Plan **out) {
     auto it = ctx->plans.find(prec * 64 + B);
     if (it != ctx->plans.end()) { *out = &it->second; return FTK_OK; }
-    // default: all columns in one launch (at most hv_max_b), the largest tile
-    const int bc = std::min(B, hv_max_b(prec));
+    // default: all columns in one launch (at most hv_max_b), the largest tile;
+    // the FP32 products of a relaxed double-float solve: one column per
+    // launch (the largest tile, fewest passes)
+    const int bc = (prec == FTK_FP32 && ctx->prec == FTK_DF) ? 1 : std::min(B, hv_max_b(prec));
     const int tb_max = hv_max_tile_bits(prec, bc);
     int tb = ctx->tile_bits_req > 0 ? std::min(ctx->tile_bits_req, tb_max) : tb_max;
     tb = std::max(2, std::min(tb, ctx->n));
@@ -522,6 +525,27 @@ static ftk_status cocg_iteration(ftk_ctx *ctx, int B, void *rcur, void *rprev, v
     if (ctx->prec == FTK_DF) {
         // double-float: the update r_{k-1} <- r_{k+1} of the previous step runs
         // inside the first pass of H r_{k+1} (rcur = r_k, rprev = r_{k-1})
+        if (ctx->relax > 0.0) {
+            // relaxed phase (device flag lowp): the update alone, then the
+            // FP32 H.V of the hi parts with mu from hi + lo; the
+            // double-float launches below return at once, and these while
+            // lowp is 0
+            const int *lowp = &ctx->dsmall->lowp;
+            UpdArgs u = ua;
+            u.mode = 1;
+            u.w_lo = 0;   // w of the switching step is read without its lo part
+            u.lowp = lowp;
+            u.lowp_run = 1;
+            LAUNCH(launch_cocg_update(upd_kind(ctx), B, rcur, w, rprev, u, vec_grid(ctx, ctx->dim), ctx->stream));
+            EpiArgs e1 = ea;
+            e1.lo = static_cast<const char *>(rprev) + size_t(8) * ua.lo_stride;
+            e1.lowp = lowp;
+            e1.lowp_run = 1;
+            ftk_status s1 = run_hv(ctx, FTK_FP32, B, EPI_COCG, rprev, w, e1);
+            if (s1) return s1;
+            ea.lowp = lowp;
+            ea.lowp_run = 0;
+        }
         ea.df_lo = ua.lo_stride;
         ea.fu_seed = ua.seed;
         ea.fu_rcur = static_cast<float2 *>(rcur);
@@ -587,7 +611,7 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     }
     CK(cudaMemcpyAsync(d->seed, seeds.data(), sizeof(CocgSeed) * B, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(d->inv_pi_max, 0, sizeof(d->inv_pi_max), ctx->stream));
-    CK(cudaMemsetAsync(&d->all_done, 0, sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(&d->all_done, 0, sizeof(int) * 2, ctx->stream));   // all_done, lowp
     double *om = (double *)wsp(ctx, ctx->L.omega);
     CK(cudaMemcpyAsync(om, omega, sizeof(double) * n_omega, cudaMemcpyHostToDevice, ctx->stream));
     // shift arrays: pi_prev = pi_cur = 1, p~ = 0, G = 0
@@ -633,6 +657,8 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     sa.hv = d->hv_dots;
     sa.inv_pi_max = d->inv_pi_max;
     sa.all_done = &d->all_done;
+    sa.relax = ctx->relax;
+    sa.lowp = &d->lowp;
     ShiftArgs sh{};
     sh.n_omega = n_omega;
     sh.seed_idx = mid;
@@ -811,6 +837,14 @@ ftk_status ftk_plan_info(const ftk_ctx *cctx, int32_t *n_passes, int32_t *tile_b
     if (s) return s;
     if (n_passes) *n_passes = (int)pl->passes.size();
     if (tile_bits) *tile_bits = pl->tile_bits;
+    return FTK_OK;
+}
+
+ftk_status ftk_set_relax(ftk_ctx *ctx, double theta) {
+    if (!ctx) return fail(nullptr, FTK_EINVAL, "null context");
+    if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(ctx, FTK_EINVAL, "theta must be finite and >= 0");
+    if (theta > 0.0 && ctx->prec != FTK_DF) return fail(ctx, FTK_EINVAL, "relaxation needs precision FTK_DF");
+    ctx->relax = theta;
     return FTK_OK;
 }
 

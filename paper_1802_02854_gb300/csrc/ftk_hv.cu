@@ -85,6 +85,7 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
     constexpr int E = 1 << LE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (ea.all_done && *ea.all_done) return;
+    if (ea.lowp && *ea.lowp != ea.lowp_run) return;
     const int b = pd.tile_bits;
     const int tb = b - LE;
     const int tile_n = 1 << b;
@@ -377,6 +378,7 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
     constexpr int E = 1 << LE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (ea.all_done && *ea.all_done) return;
+    if (ea.lowp && *ea.lowp != ea.lowp_run) return;
     const long long lo = ea.df_lo;
     const int b = pd.tile_bits;
     const int tb = b - LE;

@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(256)
 cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, UpdArgs ua) {
     __shared__ double red[(256 / 32) * 5];
     if (*ua.all_done) return;
+    if (ua.lowp && *ua.lowp != ua.lowp_run) return;
     const int j = blockIdx.y;
     const uint64_t n = ua.dim;
     const size_t off = (size_t)j * n;
@@ -237,9 +238,16 @@ __global__ void cocg_seed_kernel(SeedArgs sa) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int all = 1;
-        for (int q = 0; q < sa.n_rhs; ++q) all &= (sa.seed[q].done != 0);
+        int all = 1, small = 1;
+        for (int q = 0; q < sa.n_rhs; ++q) {
+            const CocgSeed &s = sa.seed[q];
+            all &= (s.done != 0);
+            if (!s.done) small &= (s.k >= 2 && s.resid < sa.relax);   // resid set from k = 1 on
+        }
         *sa.all_done = all;
+        // relaxed solve: from here on the matrix-vector products may run in
+        // FP32 (their errors enter scaled by the small residual)
+        if (sa.lowp && sa.relax > 0.0 && small && !all) *sa.lowp = 1;
     }
 }
 

@@ -23,6 +23,10 @@ struct EpiArgs {
     // of which r_{k+1} is written: fu_rnew, the pass's `in`), w_k = H r_k (the
     // pass's `out`, read before it is overwritten) and lambda split
     // (fu_lam); rho, g, |r|^2 of r_{k+1} go to fu_result[0..5).
+    // Relaxed double-float solve: the launch runs only while *lowp equals
+    // lowp_run (lowp NULL: always)
+    const int *lowp;
+    int lowp_run;
     const CocgSeed *fu_seed;
     float2 *fu_rcur;
     float2 *fu_rnew;
@@ -43,6 +47,8 @@ struct UpdArgs {
     long long w_lo;          // double-float mode: float2 offset of w's lo part (0: w is float)
     float4 *lam_split;       // mixed / double-float: lambda as (hi.re, hi.im, lo.re, lo.im), [B][dim];
                              // written by mode 0, read by mode 1
+    const int *lowp;         // relaxed solve: run only while *lowp == lowp_run (NULL: always)
+    int lowp_run;
 };
 
 struct SeedArgs {
@@ -54,6 +60,8 @@ struct SeedArgs {
     const double *hv;        // [B][FTK_HV_DOTS]
     double *inv_pi_max;      // [2][FTK_MAX_RHS] parity double buffer
     int *all_done;
+    double relax;            // relaxed solve: theta (0: off)
+    int *lowp;               // set (sticky) once every running RHS has resid < theta
 };
 
 struct ShiftArgs {

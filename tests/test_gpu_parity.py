@@ -260,7 +260,7 @@ def test_dimer_closed_form_spectrum(ftk):
     ctx.close()
 
 
-def _pipeline(ftk, prec, eta, tol, qis=(1, 3)):
+def _pipeline(ftk, prec, eta, tol, qis=(1, 3), relax=0.0):
     """mTPQ -> S^z_q probes -> shifted COCG -> reweighting, N = 12 (2x3,
     K = -1, J = 0.1), and O-DENSE-EST on the same seeded state."""
     cl = named(12)
@@ -271,6 +271,8 @@ def _pipeline(ftk, prec, eta, tol, qis=(1, 3)):
     T = np.array([0.5, 1.0, 2.0])
     dg = dense.Diag(cl, K, J)
     ctx = ftk.Context(cl, K, J, prec, max_rhs=4, n_saved=4)
+    if relax:
+        ctx.set_relax(relax)
     ctx.set_state(psi0, ell)
     ctx.tpq_step(n_steps, se)
     steps, en = ctx.shells()
@@ -280,7 +282,7 @@ def _pipeline(ftk, prec, eta, tol, qis=(1, 3)):
         for s in range(len(steps)):
             ctx.apply_op(s, 2, q, s)
         G, it, _ = ctx.shifted_cocg(list(range(len(steps))), omega, eta, tol=tol, max_iter=6000,
-                                    allow_noconv=(prec in ("fp32", "mixed")))
+                                    allow_noconv=(prec in ("fp32", "mixed") or relax > 0))
         S, tr = ctx.spectrum(G, T)
         ref = dense.dense_estimator(dg, psi0, ell, n_steps, se, 2, q, omega, eta, T)
         out.append((G, S, tr, ref, it))
@@ -313,3 +315,36 @@ def test_fp32_small_eta_error_is_bounded(ftk):
         print(f"mixed eta=0.02 spectrum rel err {rel(S, ref['S']):.3e}, G err {rel(G.ravel(), ref['G'].ravel()):.3e}, "
               f"iterations {it.tolist()}")
         assert err <= 5e-2
+
+
+@pytest.mark.parametrize("theta", [1e-2, 1e-3])
+def test_relaxed_df_pipeline(ftk, theta):
+    """Relaxed double-float solve (FP32 products once every residual is below
+    theta): the spectra stay within 1e-5 of the eigenbasis estimator at
+    eta = 0.02 (the FP32 products after the switch bound the accuracy; the
+    solver tolerance is 1e-6 here)."""
+    for G, S, tr, ref, it in _pipeline(ftk, "df", 0.02, 1e-6, relax=theta):
+        assert rel(S, ref["S"]) <= 1e-5
+        assert tr.tolist() == ref["trunc"].astype(int).tolist()
+
+
+def test_set_relax_checks(ftk):
+    """ftk_set_relax: negative or non-finite theta, and theta > 0 outside the
+    double-float mode, are rejected."""
+    cl = named(8)
+    for prec in ("fp64", "df"):
+        ctx = ftk.Context(cl, -1.0, 0.1, prec, max_rhs=1, n_saved=1)
+        try:
+            with pytest.raises(Exception):
+                ctx.set_relax(-1.0)
+            with pytest.raises(Exception):
+                ctx.set_relax(float("nan"))
+            if prec == "df":
+                ctx.set_relax(0.01)
+                ctx.set_relax(0.0)
+            else:
+                with pytest.raises(Exception):
+                    ctx.set_relax(0.01)
+                ctx.set_relax(0.0)
+        finally:
+            ctx.close()
