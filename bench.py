@@ -7,7 +7,7 @@ ftk_suggest_order. One step = one pass of the whole hot path over one batch:
   * S^z and S^x at momentum Q1 on both shells (4 probes)
   * one blocked shifted-COCG solve of the 4 probes in the double-float mode
     (H.V and Krylov vectors as float hi + lo pairs on the FP32 pipe, ~48
-    bits), 1024 shifts on [-3, 3], eta = 0.02, to the paper's residual 1e-4;
+    bits), 1024 shifts on [-3, 3], eta = 0.01, to the paper's residual 1e-4;
     block plan chosen by ftk_autotune (--solve-prec picks another mode)
   * the two spectra (S^z, S^x at Q1) reweighted over the shells to 32
     temperatures in [0.005, 2]
@@ -42,9 +42,9 @@ from ftk_inputs import named, omega_grid, log_temperatures, relabel  # noqa: E40
 N_SITES = 24
 K_COUPLING, J_COUPLING, ELL = -1.0, 0.05, 0.5
 TPQ_STEPS, SAVE_EVERY = 21, 20
-N_OMEGA, W_MIN, W_MAX, ETA = 1024, -3.0, 3.0, 0.02
+N_OMEGA, W_MIN, W_MAX, ETA = 1024, -3.0, 3.0, 0.01
 N_T = 32
-TOL, MAX_ITER = 1e-4, 6000
+TOL, MAX_ITER = 1e-4, 12000
 METRIC = "H·v GB/s vs HBM peak at N=24; spectra/s at 1e-5 err vs plain FP64; p50/p99"
 SOLVE_BYTES = {"fp64": 16, "df": 16, "mixed": 8, "fp32": 8}   # bytes per amplitude of a COCG H.v
 DTYPE = {"fp64": "f64", "df": "f32x2 (double-float) H.v and Krylov vectors, f64 scalars",
@@ -55,6 +55,10 @@ DTYPE = {"fp64": "f64", "df": "f32x2 (double-float) H.v and Krylov vectors, f64 
 # lo update: 8)
 DF_OPS_PER_TERM = 24
 FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070
+FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes (read + write) of one double-float H.v of one column at N = 24
+# (4 passes), from the ncu capture summarised in profiles/hv_pass_df_n24.md
+DF_HV_TRAFFIC_PER_COLUMN = 2754e6
 
 
 def peaks():
@@ -212,6 +216,7 @@ def run_gpu(args):
     l0 = ctx.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     S_fast = None
+    step_iters = []
     with Clocks() as clk:
         torch.cuda.synchronize()
         for s in range(args.steps):
@@ -219,6 +224,7 @@ def run_gpu(args):
             it, G, S = run_step(ctx, cl, omega, temps, 1000 + s, rank)
             ev[s][1].record(stream)
             iters_tot += int(np.max(it))
+            step_iters.append(it.tolist())
             if s == 0:
                 S_fast = S
         torch.cuda.synchronize()
@@ -244,7 +250,8 @@ def run_gpu(args):
         alu_peak = FP32_LANES_PER_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": round(ops / t_hv / 1e12, 3), "peak": round(alu_peak, 2),
                 "unit": "Tops/s (FP32 pipe, an FMA counts once)", "frac": round(ops / t_hv / 1e12 / alu_peak, 4),
-                "traffic": None, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                "traffic": (n_rhs * DF_HV_TRAFFIC_PER_COLUMN if N_SITES == 24 else None),
+                "traffic_unit": "DRAM bytes per launch set (ncu, profiles/hv_pass_df_n24.md)", "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
                 "kernel": f"hv_pass_df_kernel (double-float H.v, {n_rhs} columns, one per launch; tile "
                           f"2^{tile_bits}, {n_pass} passes)",
                 "ops_per_launch_set": ops, "hv_us": round(t_hv * 1e6, 2),
@@ -263,6 +270,18 @@ def run_gpu(args):
     t_hv1 = time_hv(ctx1, torch, 1, torch.complex64)
     p1 = ctx1.plan_info()
     ctx1.close()
+    # the FP64 H.v (mTPQ and the plain FP64 solve) against the FP64 pipe:
+    # 2 DFMA (4 flops) per amplitude and term (bonds + diagonal)
+    ctx2 = ftk.Context(cl, K_COUPLING, J_COUPLING, "fp64", max_rhs=1)
+    t_hv64 = time_hv(ctx2, torch, 1, torch.complex128)
+    p64 = ctx2.plan_info()
+    ctx2.close()
+    fl64 = dim * (len(cl.bonds) + 1) * 4
+    roof["hv_fp64_b1"] = {"us": round(t_hv64 * 1e6, 2), "gbs": round(2 * dim * 16 / t_hv64 / 1e9, 2),
+                          "hbm_frac": round(2 * dim * 16 / t_hv64 / 1e9 / peak, 4),
+                          "tflops": round(fl64 / t_hv64 / 1e12, 3),
+                          "fp64_frac": round(fl64 / t_hv64 / 1e12 / FP64_PEAK_TFLOPS, 4),
+                          "fp64_peak": FP64_PEAK_TFLOPS, "fp64_peak_kind": "nominal GB300 FP64", "passes": p64[0]}
     roof["hv_fp32_b1"] = {"us": round(t_hv1 * 1e6, 2), "gbs": round(2 * dim * 8 / t_hv1 / 1e9, 2),
                           "frac": round(2 * dim * 8 / t_hv1 / 1e9 / peak, 4), "peak": peak,
                           "peak_kind": peak_kind, "passes": p1[0]}
@@ -287,14 +306,18 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
         "config": {"workload": f"honeycomb24 FTKw, {prec} solve: 3x4 torus, K=-1, J=0.05, dim 2^24; 21 FP64 "
                                "mTPQ steps (shells k=0,20); S^z and S^x at Q1 on both shells = 4 RHS in one "
-                               f"blocked COCG ({DTYPE[prec]}); 1024 shifts on [-3,3], eta=0.02, "
+                               f"blocked COCG ({DTYPE[prec]}); 1024 shifts on [-3,3], eta=0.01, "
                                "tol 1e-4; 2 spectra x 32 T in [0.005,2]",
                    "n_sites": N_SITES, "n_rhs": n_rhs, "n_omega": N_OMEGA, "n_T": N_T, "solve_precision": prec,
                    "site_order": "ftk_suggest_order", "autotune": tuned,
                    "l2": "inputs larger than L2 (128-256 MiB per vector)", "parallelism": f"replicas{world}"},
         "spectra_per_s": round(spectra_per_s, 4),
         "plain_fp64": {"spectra_per_s": round(len(KINDS) / t64, 4), "seconds": round(t64, 3),
-                       "krylov_iters": it64.tolist(), "speedup": round(spectra_per_s / world / (len(KINDS) / t64), 2)},
+                       "seed": 1000, "krylov_iters": it64.tolist(),
+                       "speedup": round(spectra_per_s / world / (len(KINDS) / t64), 2),
+                       "speedup_same_seed": round(t64 / times[0], 2),
+                       "note": "FP64 runs the seed of timed step 0 only; speedup_same_seed = its time / step 0's"},
+        "krylov_iters_by_step": step_iters,
         "spectrum_rel_err_vs_fp64": {"max": err, "per_spectrum": errs,
                                      "norm": "||S - S_fp64||_2 / ||S_fp64||_2 over (omega, T)"},
         "latency_s": {"p50": round(float(np.percentile(times, 50)), 4),
@@ -420,7 +443,7 @@ def run_hv_only(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
