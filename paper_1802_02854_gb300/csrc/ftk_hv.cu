@@ -379,6 +379,7 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (ea.all_done && *ea.all_done) return;
     if (ea.lowp && *ea.lowp != ea.lowp_run) return;
+    if (ea.fu_seed && ea.fu_seed->done != 0) return;   // finished column (COCG): no work
     const long long lo = ea.df_lo;
     const int b = pd.tile_bits;
     const int tb = b - LE;

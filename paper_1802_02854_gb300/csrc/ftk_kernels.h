@@ -22,7 +22,8 @@ struct EpiArgs {
     // r_{k+1} is computed tile by tile from r_k (fu_rcur), r_{k-1} (in place
     // of which r_{k+1} is written: fu_rnew, the pass's `in`), w_k = H r_k (the
     // pass's `out`, read before it is overwritten) and lambda split
-    // (fu_lam); rho, g, |r|^2 of r_{k+1} go to fu_result[0..5).
+    // (fu_lam); rho, g, |r|^2 of r_{k+1} go to fu_result[0..5). Every pass
+    // of a column whose fu_seed is done returns at once.
     // Relaxed double-float solve: the launch runs only while *lowp equals
     // lowp_run (lowp NULL: always)
     const int *lowp;
