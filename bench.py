@@ -164,6 +164,14 @@ def run_step(ctx, cl, omega, temps, seed, sample, slots=None):
     return iters, G, S
 
 
+def products(iters, prec):
+    """H.v products of one blocked solve: in the double-float mode a finished
+    column stops its products; the other modes run every column of the block
+    until the last one finishes."""
+    it = np.asarray(iters)
+    return int(it.sum()) if prec == "df" else int(it.max()) * it.size
+
+
 def time_hv(ctx, torch, n_rhs, dt, reps=10, rows=None):
     """Average time of one H.V (all passes) of n_rhs vectors, CUDA events on
     the context stream; inputs larger than L2. rows: vector rows of the
@@ -217,6 +225,7 @@ def run_gpu(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     S_fast = None
     step_iters = []
+    prods_tot = 0
     with Clocks() as clk:
         torch.cuda.synchronize()
         for s in range(args.steps):
@@ -224,6 +233,7 @@ def run_gpu(args):
             it, G, S = run_step(ctx, cl, omega, temps, 1000 + s, rank)
             ev[s][1].record(stream)
             iters_tot += int(np.max(it))
+            prods_tot += products(it, prec)
             step_iters.append(it.tolist())
             if s == 0:
                 S_fast = S
@@ -237,7 +247,7 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt.item())
     # algorithmic H.v bytes of the steps: FP64 mTPQ products + COCG products
-    hv_bytes = args.steps * TPQ_STEPS * 2 * dim * 16 + iters_tot * n_rhs * 2 * dim * es
+    hv_bytes = args.steps * TPQ_STEPS * 2 * dim * 16 + prods_tot * 2 * dim * es
     value = world * hv_bytes / t_total / 1e9
     spectra_per_s = world * args.steps * len(KINDS) / t_total
 
@@ -362,7 +372,7 @@ def run_e2e(ctx, cl, omega, temps, args, es):
                                      allow_noconv=True)
         for p in range(len(KINDS)):
             ctx.spectrum(np.stack([G[2 * p], G[2 * p + 1]]), temps)
-        hv_bytes += TPQ_STEPS * 2 * cl.dim * 16 + int(np.max(it)) * n_rhs * 2 * cl.dim * es
+        hv_bytes += TPQ_STEPS * 2 * cl.dim * 16 + products(it, args.solve_prec) * 2 * cl.dim * es
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return {"value": round(hv_bytes / dt / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": int(cl.dim * 16),
