@@ -46,7 +46,7 @@ class JobSpec:
     omega: tuple = (-3.0, 3.0, 256)   # (min, max, count), endpoints included
     eta: float = 0.02
     temps: list = field(default_factory=lambda: [0.1, 0.5, 1.0])
-    precision: str = "fp64"           # "fp64", "fp32" or "mixed"
+    precision: str = "fp64"           # "fp64", "fp32", "mixed" or "df"
     tol: float = 1e-4
     max_iter: int = 10000
     block: int = 4

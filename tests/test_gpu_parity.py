@@ -348,3 +348,55 @@ def test_set_relax_checks(ftk):
                 ctx.set_relax(0.0)
         finally:
             ctx.close()
+
+
+def _bench_cluster_n24(ftk):
+    """The 24-site cluster with the site labels the bench uses."""
+    cl0 = named(24)
+    perm, _ = ftk.ftk_suggest_order(24, cl0.bonds, ftk.FTK_FP32, 1)
+    return relabel(cl0, perm)
+
+
+def test_hv_full_size_n24_df(ftk):
+    """Double-float H.v at full size in the bench's launch configuration
+    (relabelled sites, one column per launch, 4 passes of 2^12 tiles): every
+    element against the oracle, FP64-class accuracy."""
+    import torch
+    cl = _bench_cluster_n24(ftk)
+    vs = random_vectors(24, 1, 91)
+    hi = vs.astype(np.complex64)
+    lo = (vs - hi.astype(np.complex128)).astype(np.complex64)
+    ctx = ftk.Context(cl, -1.0, 0.05, "df", max_rhs=1)
+    out = ctx.hv(torch.from_numpy(np.concatenate([hi, lo])).cuda().contiguous())
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    n_pass, tile_bits = ctx.plan_info()
+    ctx.close()
+    got = o[0].astype(np.complex128) + o[1].astype(np.complex128)
+    assert (n_pass, tile_bits) == (4, 12)
+    assert rel(got, sparse.hv(cl, -1.0, 0.05, vs[0])) <= 1e-12
+
+
+def test_df_cocg_full_size_n24(ftk):
+    """24-site blocked solve as the bench runs it (relabelled sites, 4 RHS:
+    S^z and S^x at Q1 on two mTPQ shells, fused double-float update) against
+    the FP64 GPU solve of the same probes (pinned to the oracle at N <= 12, its
+    H.v at N = 24): G within 1e-6 at eta = 0.2, tol 1e-9; and Im G <= 0 at
+    every shift (Im z > 0), a property of the resolvent at any size."""
+    cl = _bench_cluster_n24(ftk)
+    K, J = -1.0, 0.05
+    omega = omega_grid(-3, 3, 128)
+    res = {}
+    for prec in ("df", "fp64"):
+        ctx = ftk.Context(cl, K, J, prec, max_rhs=4, n_saved=2)
+        ctx.tpq_init(7, 0, 0.5)
+        ctx.tpq_step(21, 20)
+        for slot, (sh, g) in enumerate([(0, 2), (1, 2), (0, 0), (1, 0)]):
+            ctx.apply_op(sh, g, cl.momenta[1], slot)
+        G, it, _ = ctx.shifted_cocg([0, 1, 2, 3], omega, 0.2, tol=1e-9, max_iter=4000)
+        res[prec] = G
+        ctx.close()
+    for j in range(4):
+        g = res["df"][j]
+        assert rel(g, res["fp64"][j]) <= 1e-6
+        assert (g.imag <= 1e-12 * np.abs(g).max()).all()
