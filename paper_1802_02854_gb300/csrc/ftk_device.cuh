@@ -191,21 +191,57 @@ __device__ __forceinline__ DfStep df_step(const CocgSeed &s) {
     return {{dfl_from(s.zs_re), dfl_from(s.zs_im)}, {dfl_from(s.alpha_re), dfl_from(s.alpha_im)},
             {dfl_from(s.c_re), dfl_from(s.c_im)}, (float)s.rescale};
 }
+// acc += a b in double-float: the hi x hi product exactly (FMA two-product)
+// plus the cross terms, added by a two-sum whose error goes to acc.lo (the
+// lo x lo term is below the pair precision). 12 FP32 operations.
+__device__ __forceinline__ void dfl_mac(dfl &acc, dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float t = acc.hi + p;
+    const float bb = t - acc.hi;
+    acc.lo += ((acc.hi - (t - bb)) + (p - bb)) + e;
+    acc.hi = t;
+}
+// Renormalised pair of an accumulator (two-sum: no ordering assumption).
+__device__ __forceinline__ dfl dfl_renorm(dfl a) { return dfl_two_sum(a.hi, a.lo); }
+
 // Three-term COCG residual (Sec. IV): A r_k = z_s r_k - w_k with w_k = H r_k,
-// r_{k+1} = r_k + c_k (r_k - r_{k-1}) - alpha_k A r_k, scaled by f.
+// r_{k+1} = r_k + c_k (r_k - r_{k-1}) - alpha_k A r_k, scaled by f. The
+// intermediate quantities are those of the formula (A r_k and r_k - r_{k-1}
+// are formed first); each real component accumulates its products with
+// dfl_mac and is renormalised once.
 __device__ __forceinline__ dcl df_next_residual(const dcl &rc, const dcl &rp, const dcl &w, const DfStep &q) {
-    dcl ar = dcl_mul(q.zs, rc);
-    ar.re = dfl_sub(ar.re, w.re);
-    ar.im = dfl_sub(ar.im, w.im);
-    dcl r = dcl_add(rc, dcl_sub(dcl_mul(q.cc, dcl_sub(rc, rp)), dcl_mul(q.al, ar)));
-    if (q.f != 1.f) r = {{r.re.hi * q.f, r.re.lo * q.f}, {r.im.hi * q.f, r.im.lo * q.f}};
-    return r;
+    dfl ar = dfl_neg(w.re), ai = dfl_neg(w.im);
+    dfl_mac(ar, q.zs.re, rc.re);
+    dfl_mac(ar, dfl_neg(q.zs.im), rc.im);
+    dfl_mac(ai, q.zs.re, rc.im);
+    dfl_mac(ai, q.zs.im, rc.re);
+    ar = dfl_renorm(ar);
+    ai = dfl_renorm(ai);
+    const dfl dr = dfl_sub(rc.re, rp.re), di = dfl_sub(rc.im, rp.im);
+    dfl nr = rc.re, ni = rc.im;
+    dfl_mac(nr, q.cc.re, dr);
+    dfl_mac(nr, dfl_neg(q.cc.im), di);
+    dfl_mac(nr, dfl_neg(q.al.re), ar);
+    dfl_mac(nr, q.al.im, ai);
+    dfl_mac(ni, q.cc.re, di);
+    dfl_mac(ni, q.cc.im, dr);
+    dfl_mac(ni, dfl_neg(q.al.re), ai);
+    dfl_mac(ni, dfl_neg(q.al.im), ar);
+    nr = dfl_renorm(nr);
+    ni = dfl_renorm(ni);
+    if (q.f != 1.f) { nr = {nr.hi * q.f, nr.lo * q.f}; ni = {ni.hi * q.f, ni.lo * q.f}; }
+    return {nr, ni};
 }
 // Per-thread sums of rho = r^T r, g = lambda^dag r (double-float: exact
-// two-products of the hi parts plus cross terms, two-sums) and |r|^2
-// (compensated float of the hi parts). l4 = (lambda hi.re, hi.im, lo.re, lo.im).
+// two-products of the hi parts plus cross terms, two-sums) and |r|^2 (float
+// of the hi parts: only the convergence test and the range guard read it).
+// l4 = (lambda hi.re, hi.im, lo.re, lo.im).
 struct DfUpdDots {
-    Acc<float> rr, ri, gr, gi, n;
+    Acc<float> rr, ri, gr, gi;
+    float n = 0.f;
     __device__ __forceinline__ void add(const dcl &r, const float4 &l4) {
         rr.fma_pair(r.re.hi, r.re.lo, r.re.hi, r.re.lo);
         rr.fma_pair(-r.im.hi, -r.im.lo, r.im.hi, r.im.lo);
@@ -214,11 +250,10 @@ struct DfUpdDots {
         gr.fma_pair(l4.y, l4.w, r.im.hi, r.im.lo);
         gi.fma_pair(l4.x, l4.z, r.im.hi, r.im.lo);
         gi.fma_pair(-l4.y, -l4.w, r.re.hi, r.re.lo);
-        n.fma2(r.re.hi, r.re.hi);
-        n.fma2(r.im.hi, r.im.hi);
+        n = fmaf(r.re.hi, r.re.hi, fmaf(r.im.hi, r.im.hi, n));
     }
     __device__ __forceinline__ void get(double (&v)[5]) const {
-        v[0] = rr.get(); v[1] = ri.get(); v[2] = gr.get(); v[3] = gi.get(); v[4] = n.get();
+        v[0] = rr.get(); v[1] = ri.get(); v[2] = gr.get(); v[3] = gi.get(); v[4] = n;
     }
 };
 
