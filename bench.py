@@ -131,6 +131,21 @@ def dist_env():
     return rank, world, local
 
 
+def job_totals(t_local, units_local, world, device):
+    """Whole-job timing over the ranks: the maximum of their timed seconds and
+    the sum of each of their unit counts (one collective each; world 1: the
+    local values)."""
+    if world == 1:
+        return float(t_local), [float(u) for u in units_local]
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    uu = torch.tensor([float(u) for u in units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), uu.tolist()
+
+
 # ---------------------------------------------------------------- GPU arm
 def bench_cluster(n=N_SITES):
     """The workload's cluster with the site labels that minimise H.v passes
@@ -238,18 +253,15 @@ def run_gpu(args):
             if s == 0:
                 S_fast = S
         torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     launches = ctx.launch_count() - l0
     times = [a.elapsed_time(b) / 1e3 for a, b in ev]
-    t_total = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
     # algorithmic H.v bytes of the steps: FP64 mTPQ products + COCG products
     hv_bytes = args.steps * TPQ_STEPS * 2 * dim * 16 + prods_tot * 2 * dim * es
-    value = world * hv_bytes / t_total / 1e9
-    spectra_per_s = world * args.steps * len(KINDS) / t_total
+    t_total, (hv_all, spectra_all) = job_totals(sum(times), [hv_bytes, args.steps * len(KINDS)], world, "cuda")
+    value = hv_all / t_total / 1e9
+    spectra_per_s = spectra_all / t_total
 
     # dominant kernel: the blocked H.V of the solve (autotuned plan), alone
     peak, peak_kind = peaks()
