@@ -327,8 +327,8 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
 // Double-float H.V (precision mode FTK_DF): FP64-class accuracy on the FP32
 // pipe, which on GB300 issues 64x the FP64 rate. A vector is a pair of float
 // arrays, hi and lo (lo df_lo float2 elements after hi), value hi + lo
-// (~48 significant bits). The tile holds hi and lo in separate shared-memory
-// arrays; a bond adds c * p with the exact FMA two-product of the hi parts,
+// (~48 significant bits). The tile holds an amplitude's hi and lo parts
+// together (one float4); a bond adds c * p with the exact FMA two-product of the hi parts,
 // the cross terms, and Knuth's two-sum into an accumulator (hi, lo) whose lo
 // part collects the rounding errors (renormalised when stored). One column
 // per launch, E = 2^LE amplitudes per thread, same tiling, groups and
@@ -387,9 +387,11 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
     const int T = 1 << tb;
     const int t = threadIdx.x;
     const bool act = t < T;
-    float2 *bh0 = reinterpret_cast<float2 *>(smem_raw);
-    float2 *bl0 = bh0 + tile_n, *bh1 = bl0 + tile_n, *bl1 = bh1 + tile_n, *pbh = bl1 + tile_n, *pbl = pbh + tile_n;
-    double *red = reinterpret_cast<double *>(pbl + tile_n);
+    // tile buffers of (hi.re, hi.im, lo.re, lo.im): one 16-byte shared load
+    // per partner amplitude
+    float4 *b0 = reinterpret_cast<float4 *>(smem_raw);
+    float4 *b1 = b0 + tile_n, *pb = b1 + tile_n;
+    double *red = reinterpret_cast<double *>(pb + tile_n);
 
     uint64_t st = 0;
     for (int q = 0; q < tb; ++q)
@@ -444,14 +446,15 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
     DfUpdDots udots;
     bool fdone = false;
     if constexpr (FU) fdone = ea.fu_seed->done != 0;
-    auto issue = [&](const float2 *src, long long tofs, float2 *bh, float2 *bl) {
+    auto issue = [&](const float2 *src, long long tofs, float4 *b) {
         if (act) {
             const float2 *g = src + tofs;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 const float2 *gk = g + eofs(k);
-                cp_async_elem(bh + t + T * k, gk);
-                cp_async_elem(bl + t + T * k, gk + lo);
+                float2 *d = reinterpret_cast<float2 *>(b + t + T * k);
+                cp_async_elem(d, gk);
+                cp_async_elem(d + 1, gk + lo);
             }
         }
         cp_async_commit();
@@ -460,16 +463,16 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
     long tau = blockIdx.x;
     long long tofs = tau < n_tiles ? tile_ofs(tau) : 0;
     if (tau < n_tiles) {
-        if (!FU) issue(in, tofs, bh0, bl0);
-        if (!first) issue(out, tofs, pbh, pbl);
+        if (!FU) issue(in, tofs, b0);
+        if (!first) issue(out, tofs, pb);
     }
     for (int it = 0; tau < n_tiles; tau += gridDim.x, ++it) {
-        const float2 *ch = (it & 1) ? bh1 : bh0, *cl = (it & 1) ? bl1 : bl0;
-        float2 *nh = (it & 1) ? bh0 : bh1, *nl = (it & 1) ? bl0 : bl1;
+        const float4 *cb = (it & 1) ? b1 : b0;
+        float4 *nb = (it & 1) ? b0 : b1;
         const long tn = tau + gridDim.x;
         const bool more = tn < n_tiles;
         const long long tofs_n = more ? tile_ofs(tn) : 0;
-        if (!FU && more) issue(in, tofs_n, nh, nl);
+        if (!FU && more) issue(in, tofs_n, nb);
         if (first) { if (more) cp_async_wait<1>(); else cp_async_wait<0>(); }
         else { if (more) cp_async_wait<2>(); else cp_async_wait<1>(); }
         __syncthreads();
@@ -478,7 +481,7 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
             // tile's own offsets, read before this thread overwrites them),
             // written to r_{k+1}'s buffer and to the current shared buffers
             if (act) {
-                float2 *sh = const_cast<float2 *>(ch), *sl = const_cast<float2 *>(cl);
+                float4 *sb = const_cast<float4 *>(cb);
                 float2 *rn = ea.fu_rnew + tofs, *rc = ea.fu_rcur + tofs, *wk = out + tofs;
                 const float4 *lm = ea.fu_lam + tofs;
                 if (!fdone) {
@@ -510,8 +513,7 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
                             const float2 nh2 = make_float2(r.re.hi, r.im.hi), nl2 = make_float2(r.re.lo, r.im.lo);
                             rn[e] = nh2;
                             rn[e + lo] = nl2;
-                            sh[t + T * k] = nh2;
-                            sl[t + T * k] = nl2;
+                            sb[t + T * k] = make_float4(nh2.x, nh2.y, nl2.x, nl2.y);
                             udots.add(r, l4[u]);
                         }
                     }
@@ -519,8 +521,8 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
 #pragma unroll
                     for (int k = 0; k < E; ++k) {
                         const long long e = eofs(k);
-                        sh[t + T * k] = rn[e];
-                        sl[t + T * k] = rn[e + lo];
+                        const float2 h2 = rn[e], l2 = rn[e + lo];
+                        sb[t + T * k] = make_float4(h2.x, h2.y, l2.x, l2.y);
                     }
                 }
             }
@@ -552,8 +554,9 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
                 const int tm = pd.grp_tmask[g];
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
-                    ph[k] = ch[(t ^ tm) + T * k];
-                    pl[k] = cl[(t ^ tm) + T * k];
+                    const float4 v4 = cb[(t ^ tm) + T * k];
+                    ph[k] = make_float2(v4.x, v4.y);
+                    pl[k] = make_float2(v4.z, v4.w);
                 }
                 const int pt = __popc(t & tm) & 1;
                 for (const int end = pd.grp_end[g]; q < end; ++q) {
@@ -586,7 +589,8 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
                 if (more) cp_async_wait<1>(); else cp_async_wait<0>();
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
-                    const float2 h = pbh[t + T * k], l = pbl[t + T * k];
+                    const float4 v4 = pb[t + T * k];
+                    const float2 h = make_float2(v4.x, v4.y), l = make_float2(v4.z, v4.w);
                     df_add_to(arh[k], arl[k], h.x, l.x);
                     df_add_to(aih[k], ail[k], h.y, l.y);
                 }
@@ -609,7 +613,7 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
                 }
             }
         }
-        if (!first && more) issue(out, tofs_n, pbh, pbl);
+        if (!first && more) issue(out, tofs_n, pb);
         tofs = tofs_n;
         __syncthreads();
     }
