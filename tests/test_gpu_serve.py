@@ -1,7 +1,8 @@
 """Continuous batching on the GPU: jobs of different cluster sizes,
-couplings, momenta, eta, temperatures and precisions run concurrently on
-their own streams; each result equals the same job run alone, and one job is
-checked against the oracle's eigenbasis estimator. GPU only."""
+couplings, momenta, eta, temperatures and precisions (FP64, FP32, mixed,
+double-float) run concurrently on their own streams; each result equals the
+same job run alone, and one job is checked against the oracle's eigenbasis
+estimator. GPU only."""
 import numpy as np
 import pytest
 
@@ -23,6 +24,9 @@ def _specs(serve):
         serve.JobSpec(n_sites=12, K=-1.0, J=0.0, seed=11, n_steps=11, save_every=10, probes=[(2, 2)],
                       omega=(-2, 2, 64), eta=0.08, temps=[1.0], tol=1e-8, max_iter=3000, block=2,
                       precision="mixed"),
+        serve.JobSpec(n_sites=10, K=-1.0, J=0.05, seed=13, n_steps=21, save_every=20, probes=[(2, 1), (0, 1)],
+                      omega=(-3, 3, 128), eta=0.02, temps=[0.2, 1.0], tol=1e-9, max_iter=4000, block=4,
+                      precision="df"),
     ]
 
 
