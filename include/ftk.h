@@ -16,11 +16,15 @@
  *   H.v in FP32 on the hi parts, with the COCG dot mu = r^T H r taken from
  *   hi + lo; its accuracy follows the FP32 matvec (relative 1e-7 per
  *   product), not the FP32 rounding of the recurrence. All scalar inputs and
- *   outputs are double in every mode; norms, inner products, TPQ statistics,
- *   Krylov scalars and reweighting sums are always accumulated in double.
+ *   outputs are double in every mode; TPQ statistics, Krylov scalars and
+ *   reweighting sums are computed in double; the per-thread partial sums of
+ *   norms and inner products are double (FTK_FP64), compensated float
+ *   (FTK_FP32) or double-float pairs (the COCG dots of FTK_MIXED / FTK_DF),
+ *   and are reduced across threads in double.
  *   FTK_DF is the mixed mode with H.v in double-float arithmetic on the FP32
  *   pipe (hi + lo float pairs in and out, ~48 bits): FP64-class accuracy at
- *   the FP32 pipe's issue rate. The mTPQ state is FP64 in every mode.
+ *   the FP32 pipe's issue rate; its residual update runs inside the first H.v
+ *   pass of the next step. The mTPQ state is FP64 in every mode.
  * Memory: device vectors live in ONE caller-allocated device workspace
  *   (ftk_footprint gives its size, ftk_bind_workspace hands it over); the
  *   library never allocates vector-sized memory itself. The context owns only

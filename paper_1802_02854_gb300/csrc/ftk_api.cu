@@ -513,7 +513,10 @@ ftk_status ftk_set_probe(ftk_ctx *ctx, int32_t slot, const double *v, int32_t is
 }
 
 // One blocked COCG iteration on the context stream (no host sync):
-// H R_cur -> W (+mu), seed scalars, shift recurrences, R_prev <- update.
+// H R_cur -> W (+mu), seed scalars, shift recurrences, R_prev <- update. In
+// the double-float mode the order is shifted by one step: R_prev <- update
+// of the previous step inside the first pass of H R_prev -> W (+mu), seed
+// scalars, shift recurrences (step 0 runs before the captured loop).
 // Kind of the update kernel: 0 FP64 vectors, 1 FP32 vectors, 2 mixed (split
 // float hi + lo residuals; hi at the buffer start, lo ua.lo_stride float2
 // elements later).
