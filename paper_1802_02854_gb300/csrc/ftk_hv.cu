@@ -372,7 +372,10 @@ __device__ __forceinline__ void bond_apply_df(float (&arh)[1 << LE], float (&arl
             bond_apply_df<LE, KA, KB>(arh, arl, aih, ail, ph, pl, csh, csl, cfh, cfl);               \
         break;
 
-template <int LE, int EPI, bool FU>
+// TB > 0: the thread bits of the tile (tile_bits - LE) as a compile-time
+// constant, so that the strides T k of the shared tile fold into immediate
+// offsets (the 2^12-amplitude tiles of the 24-site plans: TB = 9).
+template <int LE, int EPI, bool FU, int TB>
 __global__ void __launch_bounds__(512, 1)
 hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd, const EpiArgs ea) {
     constexpr int E = 1 << LE;
@@ -381,7 +384,7 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
     if (ea.lowp && *ea.lowp != ea.lowp_run) return;
     if (ea.fu_seed && ea.fu_seed->done != 0) return;   // finished column (COCG): no work
     const long long lo = ea.df_lo;
-    const int b = pd.tile_bits;
+    const int b = TB > 0 ? TB + LE : pd.tile_bits;
     const int tb = b - LE;
     const int tile_n = 1 << b;
     const int T = 1 << tb;
@@ -809,19 +812,20 @@ static cudaError_t attrs_b() {
 // Opt every H.V pass instantiation into the full shared memory once per
 // process (outside any stream capture); thread-safe (contexts may be created
 // from several host threads, as the server does).
-template <int LE>
+template <int LE, int TB>
 static cudaError_t attrs_df() {
-    cudaError_t e = opt_in(hv_pass_df_kernel<LE, EPI_PLAIN, false>);
-    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_COCG, false>);
-    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_PLAIN, true>);
-    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_COCG, true>);
+    cudaError_t e = opt_in(hv_pass_df_kernel<LE, EPI_PLAIN, false, TB>);
+    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_COCG, false, TB>);
+    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_PLAIN, true, TB>);
+    if (e == cudaSuccess) e = opt_in(hv_pass_df_kernel<LE, EPI_COCG, true, TB>);
     return e;
 }
 
 static cudaError_t init_attributes_once() {
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = attrs_df<3>();
-    if (e == cudaSuccess) e = attrs_df<0>();
+    if (e == cudaSuccess) e = attrs_df<3, 0>();
+    if (e == cudaSuccess) e = attrs_df<3, 9>();
+    if (e == cudaSuccess) e = attrs_df<0, 0>();
     if (e == cudaSuccess) e = attrs_b<double, 1, 3>();
     if (e == cudaSuccess) e = attrs_b<double, 2, 2>();
     if (e == cudaSuccess) e = attrs_b<double, 4, 1>();
@@ -901,13 +905,20 @@ static cudaError_t launch_chunk(int bc, int epi, const void *in, void *out, long
     }
 }
 
+template <int LE, int TB>
+static void (*df_kernel(int epi, bool fu))(const float2 *, float2 *, const PassDesc, const EpiArgs) {
+    return epi == EPI_COCG
+               ? (fu ? hv_pass_df_kernel<LE, EPI_COCG, true, TB> : hv_pass_df_kernel<LE, EPI_COCG, false, TB>)
+               : (fu ? hv_pass_df_kernel<LE, EPI_PLAIN, true, TB> : hv_pass_df_kernel<LE, EPI_PLAIN, false, TB>);
+}
+
 template <int LE>
 static cudaError_t launch_df_le(int epi, const void *in, void *out, const PassDesc &pd, const EpiArgs &ea,
                                 int grid_cap, cudaStream_t st) {
     const bool fu = ea.fu_seed != nullptr && pd.first;
-    void (*k)(const float2 *, float2 *, const PassDesc, const EpiArgs) =
-        epi == EPI_COCG ? (fu ? hv_pass_df_kernel<LE, EPI_COCG, true> : hv_pass_df_kernel<LE, EPI_COCG, false>)
-                        : (fu ? hv_pass_df_kernel<LE, EPI_PLAIN, true> : hv_pass_df_kernel<LE, EPI_PLAIN, false>);
+    void (*k)(const float2 *, float2 *, const PassDesc, const EpiArgs) = df_kernel<LE, 0>(epi, fu);
+    if constexpr (LE == 3)
+        if (pd.tile_bits == 12) k = df_kernel<LE, 9>(epi, fu);
     const int threads = hv_threads(pd);
     const size_t smem = hv_smem_bytes(2, 1, pd);
     int per_sm = 0, dev = 0, n_sm = 0;
