@@ -58,7 +58,7 @@ FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one double-float H.v of one column at N = 24
 # (4 passes), from the ncu capture summarised in profiles/hv_pass_df_n24.md
-DF_HV_TRAFFIC_PER_COLUMN = 2754e6
+DF_HV_TRAFFIC_PER_COLUMN = 2756e6
 
 
 def peaks():
