@@ -444,11 +444,8 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
     }
     Acc<float> dot[2];
     const bool first = pd.first != 0;
-    // fused residual update (first pass only): a frozen column keeps its
-    // stale residual and produces zero dots
+    // fused residual update (first pass only; a finished column returned above)
     DfUpdDots udots;
-    bool fdone = false;
-    if constexpr (FU) fdone = ea.fu_seed->done != 0;
     auto issue = [&](const float2 *src, long long tofs, float4 *b) {
         if (act) {
             const float2 *g = src + tofs;
@@ -487,7 +484,7 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
                 float4 *sb = const_cast<float4 *>(cb);
                 float2 *rn = ea.fu_rnew + tofs, *rc = ea.fu_rcur + tofs, *wk = out + tofs;
                 const float4 *lm = ea.fu_lam + tofs;
-                if (!fdone) {
+                {
                     const DfStep qs = df_step(*ea.fu_seed);
                     // loads of KB elements first (independent, in flight
                     // together), then their arithmetic and stores
@@ -520,20 +517,13 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
                             udots.add(r, l4[u]);
                         }
                     }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < E; ++k) {
-                        const long long e = eofs(k);
-                        const float2 h2 = rn[e], l2 = rn[e + lo];
-                        sb[t + T * k] = make_float4(h2.x, h2.y, l2.x, l2.y);
-                    }
                 }
             }
             __syncthreads();
             // the next tile's update inputs to L2 while this tile's bonds run
             // (one prefetch per 128-byte line: every 16th lane for float2
             // arrays, every 8th for the float4 lambda)
-            if (act && more && !fdone) {
+            if (act && more) {
                 const int lane = t & 31;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {

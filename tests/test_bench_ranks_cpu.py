@@ -64,3 +64,14 @@ def test_reference_arm_prints_on_rank0_only(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(args)
     assert buf.getvalue() == ""
+
+
+def test_products_per_mode():
+    """H.v products of a blocked solve: double-float columns stop at their own
+    convergence, the multi-column modes run every column to the last one."""
+    sys.path.insert(0, ROOT)
+    import bench
+    it = [5294, 4647, 5288, 4651]
+    assert bench.products(it, "df") == sum(it)
+    for prec in ("fp64", "mixed", "fp32"):
+        assert bench.products(it, prec) == 4 * 5294
