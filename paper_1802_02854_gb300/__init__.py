@@ -293,7 +293,9 @@ class Context:
         if workspace is None:
             workspace = torch.empty(self.bytes, dtype=torch.uint8, device="cuda")
         self.workspace = workspace
-        torch.cuda.synchronize()
+        # the allocating stream only (a device-wide synchronise would fail
+        # while another thread's context captures its solve graph)
+        torch.cuda.current_stream().synchronize()
         ftk_bind_workspace(self.handle, workspace.data_ptr(), workspace.numel())
 
     # thin method forms of the C calls

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -200,8 +201,19 @@ ftk_status run_hv(ftk_ctx *ctx, int prec, int B, int epi, const void *in, void *
     return FTK_OK;
 }
 
+// One process-wide lock for the device calls that synchronise the whole
+// device (cudaMalloc / cudaFree of the context buffers) and for the capture
+// window of the COCG graph: contexts of different host threads (the server
+// runs one per job) must not free or allocate while another thread's stream
+// is being captured.
+std::mutex &device_mu() {
+    static std::mutex m;
+    return m;
+}
+
 ftk_status ensure_stats(ftk_ctx *ctx, int need) {
     if (need <= ctx->stats_cap) return FTK_OK;
+    std::lock_guard<std::mutex> lk(device_mu());
     int cap = std::max(need, std::max(1024, ctx->stats_cap * 2));
     double *nb = nullptr;
     CK(cudaMalloc(&nb, size_t(3) * cap * sizeof(double)));
@@ -293,16 +305,18 @@ ftk_status ftk_create(const ftk_lattice *lat, const ftk_bond *bonds, int32_t n_b
         if (e != cudaSuccess) { delete ctx; return fail(nullptr, FTK_ECUDA, cudaGetErrorString(e)); }
         ctx->own_stream = true;
     }
+    std::unique_lock<std::mutex> lk(device_mu());
     e = cudaMalloc(&ctx->dsmall, sizeof(Small));
     if (e == cudaSuccess) e = cudaMemset(ctx->dsmall, 0, sizeof(Small));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->shell_scale, sizeof(double) * ctx->n_saved_cap);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->slot_energy, sizeof(double) * ctx->max_rhs);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->slot_norm2, sizeof(double) * ctx->max_rhs);
+    const cudaError_t ka = e == cudaSuccess ? init_kernel_attributes() : cudaSuccess;
+    lk.unlock();   // ftk_destroy takes the lock itself
     if (e != cudaSuccess) { ftk_destroy(ctx); return fail(nullptr, FTK_ECUDA, cudaGetErrorString(e)); }
-    e = init_kernel_attributes();
-    if (e != cudaSuccess) {
+    if (ka != cudaSuccess) {
         ftk_destroy(ctx);
-        return fail(nullptr, FTK_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+        return fail(nullptr, FTK_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(ka));
     }
     Plan *pl = nullptr;
     if (get_plan(ctx, ctx->mprec, 1, &pl) != FTK_OK) {
@@ -696,17 +710,22 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const int64_t l0 = ctx->launches;
-    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    ftk_status cs = cocg_iteration(ctx, B, rcur, rprev, w, ea, sa, sh, ua);
-    if (cs == FTK_OK) cs = cocg_iteration(ctx, B, rprev, rcur, w, ea, sa, sh, ua);
-    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
-    if (cs != FTK_OK) { if (graph) cudaGraphDestroy(graph); return cs; }
-    CK(ce);
-    const int64_t per_graph = ctx->launches - l0;
-    ctx->launches = l0;
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    CK(ce);
+    int64_t per_graph = 0;
+    cudaError_t ce = cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lk(device_mu());
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        ftk_status cs = cocg_iteration(ctx, B, rcur, rprev, w, ea, sa, sh, ua);
+        if (cs == FTK_OK) cs = cocg_iteration(ctx, B, rprev, rcur, w, ea, sa, sh, ua);
+        ce = cudaStreamEndCapture(ctx->stream, &graph);
+        if (cs != FTK_OK) { if (graph) cudaGraphDestroy(graph); return cs; }
+        CK(ce);
+        per_graph = ctx->launches - l0;
+        ctx->launches = l0;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ce);
+    }
     int done = 0, it = it0;
     const int chunk = 16;   // graph launches between host checks (32 iterations)
     ftk_status result = FTK_OK;
@@ -758,11 +777,17 @@ ftk_status ftk_spectrum(ftk_ctx *ctx, const double *Gh, int32_t n_shell, int32_t
         if (!(T[t] > 0)) return fail(ctx, FTK_EINVAL, "temperatures must be positive");
     double *gb = (double *)wsp(ctx, ctx->L.gbuf);
     double *tb = (double *)wsp(ctx, ctx->L.tbuf);
-    // S and trunc reuse the Krylov region as output staging
+    // S and trunc are staged in the Krylov region or, for small clusters,
+    // behind the G input in its staging region
+    const size_t s_need = size_t(n_T) * n_omega * 8 + n_T * 4 + 16;
+    const size_t g_used = align_up(size_t(16) * n_shell * n_omega);
     double *sb = (double *)wsp(ctx, ctx->L.kry[0]);
+    if (ctx->L.vec_bytes * ctx->max_rhs < s_need) {
+        if (g_used + s_need > ctx->L.tbuf - ctx->L.gbuf)
+            return fail(ctx, FTK_ENOMEM, "no workspace region large enough to stage the spectrum");
+        sb = (double *)wsp(ctx, ctx->L.gbuf + g_used);
+    }
     int *trb = (int *)(sb + size_t(n_T) * n_omega);
-    if (ctx->L.vec_bytes * ctx->max_rhs < size_t(n_T) * n_omega * 8 + n_T * 4 + 16)
-        return fail(ctx, FTK_ENOMEM, "Krylov region too small to stage the spectrum");
     CK(cudaMemcpyAsync(gb, Gh, size_t(16) * n_shell * n_omega, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(tb, T, sizeof(double) * n_T, cudaMemcpyHostToDevice, ctx->stream));
     SpecArgs sp{};
@@ -937,6 +962,7 @@ const char *ftk_last_error(const ftk_ctx *ctx) { return ctx ? ctx->err.c_str() :
 void ftk_destroy(ftk_ctx *ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    std::lock_guard<std::mutex> lk(device_mu());
     if (ctx->dsmall) cudaFree(ctx->dsmall);
     if (ctx->stats) cudaFree(ctx->stats);
     if (ctx->shell_scale) cudaFree(ctx->shell_scale);

@@ -286,3 +286,64 @@ class Server:
             self._mem_used -= need
             del self._running[jid]
             self._lock.notify_all()
+
+
+# ------------------------------------------------------------------ stream
+def poisson_stream(n_jobs, seed=1234, rate=2.0, sizes=(12, 16, 18, 20), precisions=("fp64", "df")):
+    """Seeded synthetic job stream of the serving workload, scaled to one GPU
+    and minutes: Poisson arrivals at `rate` jobs/s; per job a cluster size from
+    `sizes`, K = -1, J ~ U[-0.3, 0.3], one or two probes (random spin component
+    and momentum), eta in {0.01, 0.02}, 16-64 temperatures in [0.005, 2],
+    256-1024 shifts on [-3, 3], a precision from `precisions`. Returns a list of
+    (arrival offset in s, JobSpec)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for i in range(n_jobs):
+        t += rng.exponential(1.0 / rate)
+        n = int(rng.choice(sizes))
+        n_mom = n // 2
+        probes = [(int(rng.integers(0, 3)), int(rng.integers(0, n_mom))) for _ in range(int(rng.integers(1, 3)))]
+        n_t = int(rng.integers(16, 65))
+        spec = JobSpec(n_sites=n, K=-1.0, J=float(rng.uniform(-0.3, 0.3)), seed=int(rng.integers(1, 2**31)),
+                       n_steps=21, save_every=20, probes=probes,
+                       omega=(-3.0, 3.0, int(rng.choice([256, 512, 1024]))),
+                       eta=float(rng.choice([0.01, 0.02])),
+                       temps=list(np.geomspace(0.005, 2.0, n_t)), precision=str(rng.choice(precisions)),
+                       tol=1e-4, max_iter=12000, block=4)
+        out.append((t, spec))
+    return out
+
+
+def main(argv=None):
+    """Replays poisson_stream through a Server on cuda:0 and prints its stats
+    (p50/p99 latency, spectra/s, peak concurrency and memory) as one JSON line."""
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--jobs", type=int, default=40)
+    ap.add_argument("--seed", type=int, default=1234)
+    ap.add_argument("--rate", type=float, default=2.0, help="arrivals per second")
+    ap.add_argument("--slots", type=int, default=4)
+    args = ap.parse_args(argv)
+    from . import build
+    build.build()
+    stream = poisson_stream(args.jobs, args.seed, args.rate)
+    srv = Server(max_slots=args.slots)
+    t0 = time.perf_counter()
+    for off, spec in stream:
+        wait = t0 + off - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        srv.submit(spec)
+    res = srv.drain(timeout=3600)
+    srv.close()
+    st = srv.stats()
+    st.update({"jobs_submitted": args.jobs, "rate_per_s": args.rate, "slots": args.slots, "seed": args.seed,
+               "statuses": sorted({r.status for r in res}),
+               "wall_s": round(time.perf_counter() - t0, 3)})
+    print(json.dumps(st), flush=True)
+
+
+if __name__ == "__main__":
+    main()

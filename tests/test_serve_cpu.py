@@ -106,3 +106,17 @@ def test_submit_after_close_raises():
     srv.close()
     with pytest.raises(RuntimeError):
         srv.submit(JobSpec(n_sites=4))
+
+
+def test_poisson_stream_is_seeded_and_in_range():
+    from paper_1802_02854_gb300 import serve
+    a = serve.poisson_stream(30, seed=7, rate=3.0)
+    b = serve.poisson_stream(30, seed=7, rate=3.0)
+    assert [(t, s.n_sites, s.J, s.precision) for t, s in a] == [(t, s.n_sites, s.J, s.precision) for t, s in b]
+    ts = [t for t, _ in a]
+    assert all(t1 > t0 for t0, t1 in zip(ts, ts[1:]))
+    for _, s in a:
+        assert s.n_sites in (12, 16, 18, 20) and -0.3 <= s.J <= 0.3 and s.eta in (0.01, 0.02)
+        assert 16 <= len(s.temps) <= 64 and s.omega[2] in (256, 512, 1024)
+        assert all(0 <= g <= 2 and 0 <= q < s.n_sites // 2 for g, q in s.probes)
+        assert s.precision in ("fp64", "df")
