@@ -64,3 +64,33 @@ def test_create_rejects_bad_arguments(ftk, bad):
     with pytest.raises(ftk.FtkError) as e:
         ftk.ftk_create(cl.n_sites, cl.pos, bonds, -1.0, 0.1, **kw)
     assert e.value.status == ftk.FTK_EINVAL
+
+
+@pytest.mark.parametrize("n,prec,passes", [
+    (12, "fp64", 1), (12, "fp32", 1), (12, "df", 1),     # N <= tile sites: one pass, the optimum
+    (16, "fp64", 2), (16, "fp32", 2), (16, "df", 2),     # N > tile sites and every site has bonds: >= 2
+    (24, "fp32", 3), (24, "fp64", 4), (24, "df", 4),     # the 24-site plans the measurements use
+])
+def test_suggest_order_plans(ftk, n, prec, passes):
+    """Host planner (no GPU): a permutation of the sites and the number of H.v
+    passes of the relabelled cluster; deterministic (seeded restarts)."""
+    from ftk_inputs import named
+    cl = named(n)
+    perm, npass = ftk.ftk_suggest_order(n, cl.bonds, ftk.PRECISIONS[prec], 1)
+    assert sorted(perm.tolist()) == list(range(n))
+    assert npass == passes
+    perm2, npass2 = ftk.ftk_suggest_order(n, cl.bonds, ftk.PRECISIONS[prec], 1)
+    assert (perm2 == perm).all() and npass2 == npass
+
+
+def test_suggest_order_rejects_bad_arguments(ftk):
+    from ftk_inputs import named
+    cl = named(12)
+    with pytest.raises(Exception):
+        ftk.ftk_suggest_order(12, cl.bonds, ftk.FTK_FP64, 3)            # n_rhs not a power of two
+    with pytest.raises(Exception):
+        ftk.ftk_suggest_order(12, [(0, 0, 2)], ftk.FTK_FP64, 1)         # i == j
+    with pytest.raises(Exception):
+        ftk.ftk_suggest_order(12, [(0, 12, 2)], ftk.FTK_FP64, 1)        # site out of range
+    with pytest.raises(Exception):
+        ftk.ftk_suggest_order(31, cl.bonds, ftk.FTK_FP64, 1)            # more sites than supported
