@@ -14,6 +14,8 @@ Parts:
   sparse.c    matrix-free H v, mTPQ, S^gamma_q, textbook shifted COCG
               (projected and unprojected), canonical sum, Philox4x32-10.
   reweight.py reading R1: mTPQ shells to temperatures via Eq. B1.
+  ctpq.py     cTPQ state at inverse temperature beta: the Taylor series of
+              Eq. B1 in M_d steps (Appendix A).
 
 Every function is pinned by -m "not gpu" tests (tests/test_oracle_*.py)
 against closed forms, brute force, invariants and published test vectors.
