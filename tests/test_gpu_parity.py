@@ -400,3 +400,29 @@ def test_df_cocg_full_size_n24(ftk):
         g = res["df"][j]
         assert rel(g, res["fp64"][j]) <= 1e-6
         assert (g.imag <= 1e-12 * np.abs(g).max()).all()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df"])
+def test_cocg_parity_n18_vs_sparse_oracle(ftk, prec):
+    """18-site solve (3x3 torus) against the oracle's plain matrix-free
+    two-term COCG on the same probe: G at every shift within 1e-8 (both at
+    tol 1e-10, eta = 0.1); the GPU and oracle iteration counts within 5 %."""
+    cl = named(18)
+    K, J = -1.0, 0.1
+    psi0 = random_state(18, 17)
+    ctx = ftk.Context(cl, K, J, prec, max_rhs=1, n_saved=1)
+    ctx.set_state(psi0, 0.5)
+    ctx.tpq_step(1, 1)
+    steps, en = ctx.shells()
+    q = cl.momenta[2]
+    ctx.apply_op(0, 0, q, 0)
+    omega = omega_grid(-3, 3, 64)
+    eta = 0.1
+    G, it, _ = ctx.shifted_cocg([0], omega, eta, tol=1e-10, max_iter=6000)
+    ctx.close()
+    lam = sparse.apply_op(cl, 0, q, psi0)
+    z = en[0] + omega + 1j * eta
+    Gr, itr, _, st = sparse.cocg(cl, K, J, lam, z[32], z, 1e-10, 6000)
+    assert st == 0
+    assert abs(int(it[0]) - itr) <= max(10, itr // 20)
+    assert np.abs(G[0] - Gr).max() <= 1e-8 * np.abs(Gr).max()
