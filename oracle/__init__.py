@@ -16,6 +16,8 @@ Parts:
   reweight.py reading R1: mTPQ shells to temperatures via Eq. B1.
   ctpq.py     cTPQ state at inverse temperature beta: the Taylor series of
               Eq. B1 in M_d steps (Appendix A).
+  filter.py   contour filter operators, equi-energy shells, their
+              probability distribution and Green's function (Sec. II.C-D).
 
 Every function is pinned by -m "not gpu" tests (tests/test_oracle_*.py)
 against closed forms, brute force, invariants and published test vectors.
