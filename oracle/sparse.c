@@ -154,8 +154,10 @@ void orc_apply_op(int n_sites, const double *pos, int gamma, const double *q,
 
 /*
  * Shifted COCG for (z_sigma - H) chi = lambda, returning the projected
- * Green's functions G_sigma = <lambda|(z_sigma - H)^{-1}|lambda>
- * (Sec. II.B, Eq. 'linearSQomega' and the shifted Krylov paragraph).
+ * Green's functions G_sigma = <proj|(z_sigma - H)^{-1}|lambda>, proj = lambda
+ * unless given (Sec. II.B, Eq. 'linearSQomega' and the shifted Krylov
+ * paragraph; proj = A psi, lambda = B psi gives the A != B response of
+ * Eq. 'GAB_TPS').
  *
  * H is real symmetric, so z - H is complex symmetric and BiCG with the
  * shadow residual taken as conj(r) reduces to COCG: all inner products of
@@ -168,9 +170,9 @@ void orc_apply_op(int n_sites, const double *pos, int gamma, const double *q,
  *   pi_{k+1} = (1 + alpha_k D) pi_k + (alpha_k beta_{k-1}/alpha_{k-1}) (pi_k - pi_{k-1})
  *   alpha^s_k = alpha_k pi_k / pi_{k+1},  beta^s_{k-1} = (pi_{k-1}/pi_k)^2 beta_{k-1}
  *   p^s_k = r_k / pi_k + beta^s_{k-1} p^s_{k-1},   x^s_{k+1} = x^s_k + alpha^s_k p^s_k
- * Projected (unprojected == 0): only lambda^dagger p^s and G are carried.
+ * Projected (unprojected == 0): only proj^dagger p^s and G are carried.
  * Unprojected (unprojected != 0): x^s and p^s vectors are carried explicitly
- * and G = lambda^dagger x^s at the end (independent check of the projection).
+ * and G = proj^dagger x^s at the end (independent check of the projection).
  * A shift whose residual ||r_{k+1}|| / |pi^sigma_{k+1}| has dropped to
  * tol ||lambda|| is frozen (no further updates of its pi, p, G): far from the
  * seed |pi| grows geometrically and would overflow, while its remaining
@@ -180,10 +182,14 @@ void orc_apply_op(int n_sites, const double *pos, int gamma, const double *q,
  * Returns 0 converged, 1 not converged, 2 breakdown.
  */
 int orc_cocg(int n_sites, int n_bonds, const int32_t *bonds, double K, double J,
-             const cplx *lambda, double zs_re, double zs_im, int n_shift, const cplx *z,
-             double tol, int max_iter, int unprojected,
+             const cplx *lambda, const cplx *proj, double zs_re, double zs_im, int n_shift,
+             const cplx *z, double tol, int max_iter, int unprojected,
              cplx *G, int *iters_out, double *resid_out)
 {
+    /* G(z) = proj^dagger (z - H)^{-1} lambda; proj NULL: proj = lambda
+       (A = B). With proj = A psi and lambda = B psi this is the response
+       <psi|A^dagger (z - H)^{-1} B|psi> of two different operators. */
+    if (!proj) proj = lambda;
     uint64_t d = 1ull << n_sites;
     cplx z_seed = zs_re + I * zs_im;
     cplx *r = malloc(d * sizeof(cplx)), *p = calloc(d, sizeof(cplx));
@@ -210,7 +216,7 @@ int orc_cocg(int n_sites, int n_bonds, const int32_t *bonds, double K, double J,
         cplx pq = dotu(d, p, qv);
         if (cabs(pq) == 0.0 || cabs(rho) == 0.0) { status = 2; break; }
         cplx alpha = rho / pq;
-        cplx g = dotc(d, lambda, r);                       /* lambda^dagger r_k */
+        cplx g = dotc(d, proj, r);                         /* proj^dagger r_k */
         for (int s = 0; s < n_shift; ++s) {
             if (frozen[s]) continue;
             cplx dz = z[s] - z_seed;
@@ -249,7 +255,7 @@ int orc_cocg(int n_sites, int n_bonds, const int32_t *bonds, double K, double J,
     }
     (void)beta_prev;
     if (unprojected) {
-        for (int s = 0; s < n_shift; ++s) G[s] = dotc(d, lambda, xs + (size_t)s * d);
+        for (int s = 0; s < n_shift; ++s) G[s] = dotc(d, proj, xs + (size_t)s * d);
     }
     *iters_out = k;
     *resid_out = worst / (lnorm > 0 ? lnorm : 1.0);

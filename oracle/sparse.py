@@ -24,7 +24,7 @@ def lib():
                                  C.c_double, C.c_int, C.c_int, cp, cp, cp, cp]
         _lib.orc_tpq.restype = C.c_int
         _lib.orc_apply_op.argtypes = [C.c_int, cp, C.c_int, cp, cp, cp]
-        _lib.orc_cocg.argtypes = [C.c_int, C.c_int, cp, C.c_double, C.c_double, cp,
+        _lib.orc_cocg.argtypes = [C.c_int, C.c_int, cp, C.c_double, C.c_double, cp, C.c_void_p,
                                   C.c_double, C.c_double, C.c_int, cp, C.c_double, C.c_int, C.c_int,
                                   cp, cp, cp]
         _lib.orc_cocg.restype = C.c_int
@@ -75,14 +75,18 @@ def apply_op(cl, gamma, q, psi):
     return out
 
 
-def cocg(cl, K, J, lam, z_seed, z, tol, max_iter, unprojected=False):
-    """Shifted COCG; returns (G [n_shift], iters, rel_resid, status)."""
+def cocg(cl, K, J, lam, z_seed, z, tol, max_iter, unprojected=False, proj=None):
+    """Shifted COCG for (z - H) x = lam; returns (G [n_shift], iters,
+    rel_resid, status) with G = proj^dagger x (proj None: lam)."""
     lam = np.ascontiguousarray(lam, dtype=np.complex128)
+    if proj is not None:
+        proj = np.ascontiguousarray(proj, dtype=np.complex128)
     z = np.ascontiguousarray(z, dtype=np.complex128)
     G = np.empty_like(z)
     it = np.zeros(1, dtype=np.int32); res = np.zeros(1)
     b = _bonds(cl)
-    st = lib().orc_cocg(cl.n_sites, cl.n_bonds, _p(b), K, J, _p(lam), float(np.real(z_seed)), float(np.imag(z_seed)), z.size, _p(z),
+    st = lib().orc_cocg(cl.n_sites, cl.n_bonds, _p(b), K, J, _p(lam), None if proj is None else _p(proj),
+                        float(np.real(z_seed)), float(np.imag(z_seed)), z.size, _p(z),
                         tol, max_iter, int(unprojected), _p(G), _p(it), _p(res))
     return G, int(it[0]), float(res[0]), int(st)
 

@@ -118,3 +118,38 @@ def test_gaussian_state_properties():
     assert abs(np.mean(re * im)) < 0.02
     w = sparse.gaussian_state(16, 1234, 1)
     assert abs(np.vdot(v, w)) < 0.02
+
+
+@pytest.mark.parametrize("unprojected", [False, True])
+def test_cocg_two_operator_response(unprojected):
+    """A != B: G(z) = <A psi|(z - H)^{-1}|B psi> with A = S^x_q, B = S^z_q
+    against the dense resolvent sum_m <A psi|m><m|B psi> / (z - E_m)."""
+    cl = named(8)
+    K, J = -1.0, 0.1
+    dg = dense.Diag(cl, K, J)
+    psi = random_state(8, 41)
+    q = cl.momenta[1]
+    a = sparse.apply_op(cl, 0, q, psi)
+    b = sparse.apply_op(cl, 2, q, psi)
+    z = np.linspace(-2, 2, 40) + 0.1j
+    G, it, res, st = sparse.cocg(cl, K, J, b, z[20], z, 1e-12, 5000, unprojected=unprojected, proj=a)
+    assert st == 0
+    ca, cb = dg.V.T @ a, dg.V.T @ b
+    ref = np.array([np.sum(np.conj(ca) * cb / (zz - dg.E)) for zz in z])
+    assert np.max(np.abs(G - ref)) <= 1e-9 * np.abs(ref).max()
+
+
+def test_cocg_two_operator_reciprocity():
+    """(z - H)^{-1} is complex symmetric and R(z)^dagger = R(conj z), so
+    G^{AB}(z) = conj(G^{BA}(conj z)), computed by two independent solves."""
+    cl = named(8)
+    K, J = -1.0, 0.1
+    psi = random_state(8, 43)
+    q = cl.momenta[2]
+    a = sparse.apply_op(cl, 1, q, psi)
+    b = sparse.apply_op(cl, 2, q, psi)
+    z = np.linspace(-2, 2, 30) + 0.2j
+    gab, _, _, s1 = sparse.cocg(cl, K, J, b, z[15], z, 1e-12, 5000, proj=a)
+    gba, _, _, s2 = sparse.cocg(cl, K, J, a, np.conj(z[15]), np.conj(z), 1e-12, 5000, proj=b)
+    assert s1 == 0 and s2 == 0
+    assert np.max(np.abs(gab - np.conj(gba))) <= 1e-9 * np.abs(gab).max()
