@@ -59,6 +59,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one double-float H.v of one column at N = 24
 # (4 passes), from the ncu capture summarised in profiles/hv_pass_df_n24.md
 DF_HV_TRAFFIC_PER_COLUMN = 2756e6
+DF_HV_TRAFFIC_PASSES = 4        # the plan those counters were taken on
 
 
 def peaks():
@@ -149,10 +150,11 @@ def job_totals(t_local, units_local, world, device):
 # ---------------------------------------------------------------- GPU arm
 def bench_cluster(n=N_SITES):
     """The workload's cluster with the site labels that minimise H.v passes
-    (FP32 matvec, one vector per launch)."""
+    (16-byte amplitudes, one vector per launch: at N = 24 three passes for the
+    double-float and FP64 products, and three for FP32 as well)."""
     import paper_1802_02854_gb300 as ftk
     cl = named(n)
-    perm, _ = ftk.ftk_suggest_order(n, cl.bonds, ftk.FTK_FP32, 1)
+    perm, _ = ftk.ftk_suggest_order(n, cl.bonds, ftk.FTK_DF, 1)
     return relabel(cl, perm)
 
 
@@ -272,7 +274,8 @@ def run_gpu(args):
         alu_peak = FP32_LANES_PER_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": round(ops / t_hv / 1e12, 3), "peak": round(alu_peak, 2),
                 "unit": "Tops/s (FP32 pipe, an FMA counts once)", "frac": round(ops / t_hv / 1e12 / alu_peak, 4),
-                "traffic": (n_rhs * DF_HV_TRAFFIC_PER_COLUMN if N_SITES == 24 else None),
+                "traffic": (n_rhs * DF_HV_TRAFFIC_PER_COLUMN if (N_SITES, n_pass) == (24, DF_HV_TRAFFIC_PASSES)
+                            else None),
                 "traffic_unit": "DRAM bytes per launch set (ncu, profiles/hv_pass_df_n24.md)", "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
                 "kernel": f"hv_pass_df_kernel (double-float H.v, {n_rhs} columns, one per launch; tile "
                           f"2^{tile_bits}, {n_pass} passes)",

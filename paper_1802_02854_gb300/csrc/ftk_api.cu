@@ -150,7 +150,7 @@ bool plan_passes(ftk_ctx *ctx, int prec, int bc, int tile_bits, Plan &pl) {
     for (int q = 0; q < ctx->nb; ++q) pb[q] = {ctx->bonds[q].i, ctx->bonds[q].j, ctx->bonds[q].g};
     PassDesc pd[FTK_MAX_PASSES];
     const int np = plan_hv_passes(ctx->n, pb, ctx->nb, ctx->K, ctx->J, elem_bytes(prec), bc, tile_bits, pd,
-                                  FTK_MAX_PASSES, &pl.tile_bits, &pl.chunk_bits);
+                                  FTK_MAX_PASSES, &pl.tile_bits, &pl.chunk_bits, 32, kPlanLocalSteps);
     if (np == 0) return false;
     for (int p = 0; p < np; ++p)
         if (!hv_layout_pass(pd[p], prec, bc)) return false;

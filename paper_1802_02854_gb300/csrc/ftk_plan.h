@@ -3,6 +3,7 @@
 #pragma once
 #include "ftk_common.cuh"
 
+#include <math.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -82,9 +83,113 @@ inline int plan_cover(int n, const PlanBond *bonds, int nb, int b, int c, uint32
     return np;
 }
 
+// Local search for a cover with np passes: every pass holds the chunk sites
+// and b - c other sites. The chunk sites are the lowest c labels, or, with
+// joint_chunk, any c sites (searched too; returned in chunk_out). Simulated
+// annealing on the number of bonds whose two sites share a pass: seeded,
+// at most `steps` moves, no heap memory. On success (every bond covered)
+// sets[p] holds the b sites of pass p, chunk sites first.
+inline bool plan_anneal_cover(int n, const PlanBond *bonds, int nb, int b, int c, int np, uint32_t seed,
+                              long steps, bool joint_chunk, int sets[][FTK_MAX_SITES], int *chunk_out) {
+    if (np < 1 || np > FTK_MAX_PASSES || b >= n || c > b || c < 0) return false;
+    const int m = b - c;   // non-chunk sites per pass
+    if (m < 1) return false;
+    PlanRng rng{seed * 2654435761u + 0x9e3779b9u};
+    if (rng.s == 0) rng.s = 1;
+    char chunk[FTK_MAX_SITES];
+    char mem[FTK_MAX_PASSES][FTK_MAX_SITES];
+    memset(chunk, 0, sizeof chunk);
+    memset(mem, 0, sizeof mem);
+    // a uniformly drawn site with flag test() true (bounded rejection sampling)
+    auto draw = [&](auto test) -> int {
+        for (int t = 0; t < 4096; ++t) {
+            const int s = (int)(rng.next() % (uint32_t)n);
+            if (test(s)) return s;
+        }
+        for (int s = 0; s < n; ++s)
+            if (test(s)) return s;
+        return -1;
+    };
+    if (!joint_chunk) {
+        for (int s = 0; s < c; ++s) chunk[s] = 1;
+    } else {
+        for (int k = 0; k < c; ++k) chunk[draw([&](int s) { return !chunk[s]; })] = 1;
+    }
+    for (int p = 0; p < np; ++p)
+        for (int k = 0; k < m; ++k) mem[p][draw([&](int s) { return !chunk[s] && !mem[p][s]; })] = 1;
+    auto covered = [&]() {
+        int cov = 0;
+        for (int q = 0; q < nb; ++q) {
+            const int i = bonds[q].i, j = bonds[q].j;
+            for (int p = 0; p < np; ++p)
+                if ((chunk[i] || mem[p][i]) && (chunk[j] || mem[p][j])) { ++cov; break; }
+        }
+        return cov;
+    };
+    int cur = covered();
+    double T = 2.0;
+    for (long st = 0; st < steps && cur < nb; ++st) {
+        int kind, p = 0, a = -1, x = -1;
+        char moved[FTK_MAX_PASSES];
+        if (joint_chunk && c > 0 && rng.next() % 10 == 0) {
+            // a chunk site and a non-chunk site trade places (in every pass
+            // that held x, a takes its place)
+            kind = 0;
+            a = draw([&](int s) { return chunk[s] != 0; });
+            x = draw([&](int s) { return !chunk[s]; });
+            chunk[a] = 0;
+            chunk[x] = 1;
+            for (int q = 0; q < np; ++q) {
+                moved[q] = mem[q][x];
+                if (moved[q]) { mem[q][x] = 0; mem[q][a] = 1; }
+            }
+        } else {
+            // pass p swaps one of its sites for another
+            kind = 1;
+            p = (int)(rng.next() % (uint32_t)np);
+            a = draw([&](int s) { return mem[p][s] != 0; });
+            x = draw([&](int s) { return !chunk[s] && !mem[p][s]; });
+            mem[p][a] = 0;
+            mem[p][x] = 1;
+        }
+        const int nw = covered();
+        const double u = (double)(rng.next() >> 8) * (1.0 / 16777216.0);
+        if (nw >= cur || u < exp((nw - cur) / T)) {
+            cur = nw;
+        } else if (kind == 0) {
+            chunk[x] = 0;
+            chunk[a] = 1;
+            for (int q = 0; q < np; ++q)
+                if (moved[q]) { mem[q][a] = 0; mem[q][x] = 1; }
+        } else {
+            mem[p][x] = 0;
+            mem[p][a] = 1;
+        }
+        T = T * 0.9995 > 0.05 ? T * 0.9995 : 0.05;
+    }
+    if (cur < nb) return false;
+    int k = 0;
+    for (int s = 0; s < n; ++s)
+        if (chunk[s]) { if (chunk_out) chunk_out[k] = s; ++k; }
+    for (int p = 0; p < np; ++p) {
+        int t = 0;
+        for (int s = 0; s < n; ++s)
+            if (chunk[s]) sets[p][t++] = s;
+        for (int s = 0; s < n; ++s)
+            if (mem[p][s]) sets[p][t++] = s;
+    }
+    return true;
+}
+
+// Moves of one local-search restart (context plans and site relabelling; the
+// allocation-free entry point plans greedily only).
+constexpr long kPlanLocalSteps = 30000;
+
+// local_steps > 0: after the greedy covers, a local search (plan_anneal_cover,
+// 8 seeded restarts of local_steps moves) looks for covers with fewer passes.
 inline int plan_hv_passes(int n, const PlanBond *bonds, int nb, double K, double J, int elem_bytes,
                           int B, int tile_bits, PassDesc *pd, int max_passes, int *b_out, int *c_out,
-                          int restarts = 32) {
+                          int restarts = 32, long local_steps = 0) {
     if (n < 2 || n > FTK_MAX_SITES || nb < 1 || nb > 2 * FTK_MAX_PASS_BONDS) return 0;
     int c = 0;
     while (c < n && ((long)1 << c) * B * elem_bytes < 256) ++c;
@@ -107,6 +212,21 @@ inline int plan_hv_passes(int n, const PlanBond *bonds, int nb, double K, double
         if (b >= n) break;
     }
     if (best_np == 0) return 0;
+    if (local_steps > 0 && b < n) {
+        for (int target = best_np - 1; target >= 1; --target) {
+            bool found = false;
+            for (int r = 0; r < 8 && !found; ++r) {
+                int sets[FTK_MAX_PASSES][FTK_MAX_SITES];
+                if (plan_anneal_cover(n, bonds, nb, b, c, target, 1000u + (uint32_t)r, local_steps, false, sets,
+                                      nullptr)) {
+                    memcpy(best_sets, sets, sizeof sets);
+                    best_np = target;
+                    found = true;
+                }
+            }
+            if (!found) break;
+        }
+    }
     // materialise the passes: each bond goes to the first pass containing it
     char remaining[2 * FTK_MAX_PASS_BONDS];
     for (int q = 0; q < nb; ++q) remaining[q] = 1;
@@ -201,6 +321,35 @@ inline int plan_suggest_order(int n, const PlanBond *bonds, int nb, int elem_byt
             best = np;
             for (int s = 0; s < n; ++s) perm[s] = cand[s];
         }
+    }
+    // local search over the chunk sites and the passes together; a cover with
+    // fewer passes fixes the chunk sites (lowest labels, the other sites in
+    // their order after them), kept if the planner with its own local search
+    // reaches that count on the relabelled bonds
+    for (int target = best - 1; b < n && target >= 1; --target) {
+        bool found = false;
+        for (int r = 0; r < 8 && !found; ++r) {
+            int sets[FTK_MAX_PASSES][FTK_MAX_SITES], chunk[FTK_MAX_SITES];
+            if (!plan_anneal_cover(n, bonds, nb, b, c, target, 7u + (uint32_t)r, kPlanLocalSteps, true, sets, chunk))
+                continue;
+            int cand[FTK_MAX_SITES];
+            char is_chunk[FTK_MAX_SITES];
+            memset(is_chunk, 0, sizeof is_chunk);
+            for (int k = 0; k < c; ++k) { cand[chunk[k]] = k; is_chunk[chunk[k]] = 1; }
+            int next = c;
+            for (int s = 0; s < n; ++s)
+                if (!is_chunk[s]) cand[s] = next++;
+            PlanBond rb[2 * FTK_MAX_PASS_BONDS];
+            for (int q = 0; q < nb; ++q) rb[q] = {cand[bonds[q].i], cand[bonds[q].j], bonds[q].g};
+            const int np = plan_hv_passes(n, rb, nb, -1.0, 0.1, elem_bytes, B, tile_bits, pd, FTK_MAX_PASSES, &b, &c,
+                                          16, kPlanLocalSteps);
+            if (np > 0 && np <= target) {
+                best = np;
+                for (int s = 0; s < n; ++s) perm[s] = cand[s];
+                found = true;
+            }
+        }
+        if (!found) break;
     }
     return best;
 }

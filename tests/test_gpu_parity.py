@@ -353,13 +353,13 @@ def test_set_relax_checks(ftk):
 def _bench_cluster_n24(ftk):
     """The 24-site cluster with the site labels the bench uses."""
     cl0 = named(24)
-    perm, _ = ftk.ftk_suggest_order(24, cl0.bonds, ftk.FTK_FP32, 1)
+    perm, _ = ftk.ftk_suggest_order(24, cl0.bonds, ftk.FTK_DF, 1)
     return relabel(cl0, perm)
 
 
 def test_hv_full_size_n24_df(ftk):
     """Double-float H.v at full size in the bench's launch configuration
-    (relabelled sites, one column per launch, 4 passes of 2^12 tiles): every
+    (relabelled sites, one column per launch, 3 passes of 2^12 tiles): every
     element against the oracle, FP64-class accuracy."""
     import torch
     cl = _bench_cluster_n24(ftk)
@@ -373,7 +373,7 @@ def test_hv_full_size_n24_df(ftk):
     n_pass, tile_bits = ctx.plan_info()
     ctx.close()
     got = o[0].astype(np.complex128) + o[1].astype(np.complex128)
-    assert (n_pass, tile_bits) == (4, 12)
+    assert (n_pass, tile_bits) == (3, 12)
     assert rel(got, sparse.hv(cl, -1.0, 0.05, vs[0])) <= 1e-12
 
 
