@@ -144,13 +144,15 @@ void ftk::set_thread_error(const char *msg) { g_create_err = msg; }
 
 namespace {
 
-// Plan the passes of H.V for column chunks of bc right-hand sides.
-bool plan_passes(ftk_ctx *ctx, int prec, int bc, int tile_bits, Plan &pl) {
+// Plan the passes of H.V for column chunks of bc right-hand sides: the
+// planner with its local search first; if that plan cannot be laid out for
+// the kernel (or needs too much shared memory), the greedy plan alone.
+bool plan_passes_with(ftk_ctx *ctx, int prec, int bc, int tile_bits, long local_steps, Plan &pl) {
     PlanBond pb[2 * FTK_MAX_PASS_BONDS];
     for (int q = 0; q < ctx->nb; ++q) pb[q] = {ctx->bonds[q].i, ctx->bonds[q].j, ctx->bonds[q].g};
     PassDesc pd[FTK_MAX_PASSES];
     const int np = plan_hv_passes(ctx->n, pb, ctx->nb, ctx->K, ctx->J, elem_bytes(prec), bc, tile_bits, pd,
-                                  FTK_MAX_PASSES, &pl.tile_bits, &pl.chunk_bits, 32, kPlanLocalSteps);
+                                  FTK_MAX_PASSES, &pl.tile_bits, &pl.chunk_bits, 32, local_steps);
     if (np == 0) return false;
     for (int p = 0; p < np; ++p)
         if (!hv_layout_pass(pd[p], prec, bc)) return false;
@@ -159,6 +161,12 @@ bool plan_passes(ftk_ctx *ctx, int prec, int bc, int tile_bits, Plan &pl) {
     pl.smem = hv_smem_bytes(prec, bc, pl.passes[0]);
     pl.grid = 8 * ctx->n_sm;   // cap of the persistent grid (4 MB of reduction partials)
     return pl.smem <= (size_t(227) << 10);
+}
+
+bool plan_passes(ftk_ctx *ctx, int prec, int bc, int tile_bits, Plan &pl) {
+    if (plan_passes_with(ctx, prec, bc, tile_bits, kPlanLocalSteps, pl)) return true;
+    pl = Plan{};
+    return plan_passes_with(ctx, prec, bc, tile_bits, 0, pl);
 }
 
 ftk_status get_plan(ftk_ctx *ctx, int prec, int B, Plan **out) {
