@@ -426,3 +426,25 @@ def test_cocg_parity_n18_vs_sparse_oracle(ftk, prec):
     assert st == 0
     assert abs(int(it[0]) - itr) <= max(10, itr // 20)
     assert np.abs(G[0] - Gr).max() <= 1e-8 * np.abs(Gr).max()
+
+
+def test_hv_full_size_n28_fp32(ftk):
+    """28-site cluster (2x7 torus, dim 2^28, 2 GiB per FP32 vector) in the
+    mixed-precision configuration's launch configuration (FP32 H.v, sites
+    relabelled by ftk_suggest_order): every element against the oracle's
+    FP64 matrix-free H.v."""
+    import torch
+    cl0 = named(28)
+    perm, _ = ftk.ftk_suggest_order(28, cl0.bonds, ftk.FTK_FP32, 1)
+    cl = relabel(cl0, perm)
+    rng = np.random.default_rng(2828)
+    v = (rng.standard_normal(cl.dim, dtype=np.float32) + 1j * rng.standard_normal(cl.dim, dtype=np.float32))
+    v = (v / np.linalg.norm(v)).astype(np.complex64)
+    ctx = ftk.Context(cl, -1.0, 0.1, "fp32", max_rhs=1)
+    out = ctx.hv(torch.from_numpy(v).cuda())
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.complex128)
+    ctx.close()
+    del out
+    ref = sparse.hv(cl, -1.0, 0.1, v.astype(np.complex128))
+    assert rel(got, ref) <= TOL_HV["fp32"]
