@@ -185,3 +185,23 @@ def test_estimator_vs_canonical_statistically():
         assert abs(ints.mean() - want) < 3 * se + 0.02 * want
         rel = np.linalg.norm(mean[it] - canon[it]) / np.linalg.norm(canon[it])
         assert rel < 0.5, rel
+
+
+@pytest.mark.parametrize("gamma", [0, 1, 2])
+def test_detailed_balance_of_the_canonical_weights(gamma):
+    """Unbroadened canonical weights: the transition n -> m of S_q at
+    omega = E_m - E_n and the reverse transition m -> n of S_{-q} at -omega
+    satisfy W_{-q}(m -> n) = e^{-omega/T} W_q(n -> m), since
+    S^gamma_{-q} = (S^gamma_q)^dagger and p_m / p_n = e^{-(E_m - E_n)/T}."""
+    cl = named(8)
+    dg = dense.Diag(cl, -1.0, 0.1)
+    q = np.asarray(cl.momenta[1], dtype=float)
+    a_p = dg.op_eigen(gamma, q)          # <m|S_q|n>
+    a_m = dg.op_eigen(gamma, -q)         # <m|S_-q|n>
+    for T in (0.3, 1.0):
+        p = np.exp(-(dg.E - dg.E[0]) / T)
+        p /= p.sum()
+        w_fwd = np.abs(a_p) ** 2 * p[None, :]          # [m, n]: n -> m
+        w_rev = (np.abs(a_m) ** 2 * p[None, :]).T      # [m, n]: m -> n under S_-q
+        omega = dg.E[:, None] - dg.E[None, :]
+        assert np.allclose(w_rev, np.exp(-omega / T) * w_fwd, rtol=1e-10, atol=1e-14)
