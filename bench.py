@@ -132,6 +132,17 @@ def dist_env():
     return rank, world, local
 
 
+def bench_config(prec, world):
+    """The workload of one step (both arms report it)."""
+    return {"workload": f"honeycomb24 FTKw, {prec} solve: 3x4 torus, K=-1, J=0.05, dim 2^24; 21 FP64 "
+                        "mTPQ steps (shells k=0,20); S^z and S^x at Q1 on both shells = 4 RHS in one "
+                        f"blocked COCG ({DTYPE[prec]}); 1024 shifts on [-3,3], eta=0.01, "
+                        "tol 1e-4; 2 spectra x 32 T in [0.005,2]",
+            "n_sites": N_SITES, "n_rhs": len(PROBES), "n_omega": N_OMEGA, "n_T": N_T, "solve_precision": prec,
+            "site_order": "ftk_suggest_order", "l2": "inputs larger than L2 (128-256 MiB per vector)",
+            "parallelism": f"replicas{world}"}
+
+
 def job_totals(t_local, units_local, world, device):
     """Whole-job timing over the ranks: the maximum of their timed seconds and
     the sum of each of their unit counts (one collective each; world 1: the
@@ -329,13 +340,7 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * t_total / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
-        "config": {"workload": f"honeycomb24 FTKw, {prec} solve: 3x4 torus, K=-1, J=0.05, dim 2^24; 21 FP64 "
-                               "mTPQ steps (shells k=0,20); S^z and S^x at Q1 on both shells = 4 RHS in one "
-                               f"blocked COCG ({DTYPE[prec]}); 1024 shifts on [-3,3], eta=0.01, "
-                               "tol 1e-4; 2 spectra x 32 T in [0.005,2]",
-                   "n_sites": N_SITES, "n_rhs": n_rhs, "n_omega": N_OMEGA, "n_T": N_T, "solve_precision": prec,
-                   "site_order": "ftk_suggest_order", "autotune": tuned,
-                   "l2": "inputs larger than L2 (128-256 MiB per vector)", "parallelism": f"replicas{world}"},
+        "config": dict(bench_config(prec, world), autotune=tuned),
         "spectra_per_s": round(spectra_per_s, 4),
         "plain_fp64": {"spectra_per_s": round(len(KINDS) / t64, 4), "seconds": round(t64, 3),
                        "seed": 1000, "krylov_iters": it64.tolist(),
@@ -433,8 +438,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "honeycomb24 plain FTKw FP64 (oracle H.v on host cores)",
-                       "n_sites": N_SITES},
+            "config": bench_config(args.solve_prec, world),
             "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
