@@ -205,3 +205,37 @@ def test_detailed_balance_of_the_canonical_weights(gamma):
         w_rev = (np.abs(a_m) ** 2 * p[None, :]).T      # [m, n]: m -> n under S_-q
         omega = dg.E[:, None] - dg.E[None, :]
         assert np.allclose(w_rev, np.exp(-omega / T) * w_fwd, rtol=1e-10, atol=1e-14)
+
+
+def test_shell_of_step_is_the_nearest_saved_shell():
+    """Brute force: the saved shell nearest to step k, ties to the later one
+    (reading R1), clipped to the saved range."""
+    steps = [0, 20, 40, 60]
+    for k in range(0, 90):
+        d = [abs(k - s) for s in steps]
+        best = min(d)
+        want = max(i for i, x in enumerate(d) if x == best)
+        assert int(reweight.shell_of_step(k, steps)) == want
+
+
+def test_reweighted_spectrum_is_a_convex_combination():
+    """R1's shell weights are positive and sum to one: identical shell spectra
+    are returned unchanged, and any result lies between the shells' minimum
+    and maximum at every frequency."""
+    cl = named(8)
+    n = cl.n_sites
+    dg = dense.Diag(cl, -1.0, 0.1)
+    psi0 = random_state(n, 13)
+    _, u, lq, _ = dense.mtpq_eigen(dg, psi0, 0.5, 61)
+    steps = [0, 20, 40, 60]
+    rng = np.random.default_rng(3)
+    temps = [0.05, 0.3, 1.0, 3.0]
+    same = np.tile(rng.random(17), (4, 1))
+    S, _ = reweight.spectrum(n, 0.5, u, lq, steps, same, temps)
+    assert np.allclose(S, same[0][None, :], rtol=1e-13, atol=0)
+    diff = rng.random((4, 17))
+    S, _ = reweight.spectrum(n, 0.5, u, lq, steps, diff, temps)
+    assert np.all(S >= diff.min(axis=0) - 1e-14) and np.all(S <= diff.max(axis=0) + 1e-14)
+    for t in temps:
+        w, _ = reweight.shell_weights(n, 0.5, u, lq, steps, 1.0 / t)
+        assert np.all(w >= 0) and abs(w.sum() - 1.0) <= 1e-13
