@@ -203,6 +203,10 @@ ftk_status ftk_plan_info(const ftk_ctx *ctx, int32_t *n_passes, int32_t *tile_bi
  * shape (tile_bits 0 = the default). perm_out (host, n_sites ints) receives
  * site l -> new label perm_out[l]; relabel the sites (and their positions)
  * before ftk_create. n_passes_out (may be NULL) receives the pass count.
+ * The search is deterministic: seeded choices of the chunk sites with greedy
+ * covers, then a bounded local search over the chunk sites and the passes
+ * together (about 0.1 s at N = 24). Contexts plan their own passes with the
+ * same local search for fixed labels.
  * FTK_EINVAL on bad arguments (message via ftk_last_error(NULL)). */
 ftk_status ftk_suggest_order(int32_t n_sites, const ftk_bond *bonds, int32_t n_bonds, int32_t precision,
                              int32_t n_rhs, int32_t tile_bits, int32_t *perm_out, int32_t *n_passes_out);
