@@ -21,6 +21,13 @@
 // coefficient choice par/anti is resolved once per thread and bond from the
 // thread bits, and at compile time from the register bits). The group with
 // tm = 0 holds the bonds between register sites, and the diagonal.
+//
+// Two kernels: hv_pass_kernel (FP64 / FP32 amplitudes, several columns per
+// launch) and hv_pass_df_kernel (double-float amplitudes, hi + lo float
+// pairs, one column per launch; a tile amplitude's hi and lo parts side by
+// side in one float4; a variant with the tile stride as a compile-time
+// constant; a variant whose first pass also performs the COCG residual update
+// of the previous step).
 #include "ftk_common.cuh"
 #include "ftk_device.cuh"
 #include "ftk_kernels.h"

@@ -2,7 +2,11 @@
 // Hamiltonian-vector product is a bit-indexed gather, not a contraction.
 //
 //   (the H.V pass lives in ftk_hv.cu)
-//   cocg_update 3-term seed-COCG residual update with fused dots (Sec. II.B)
+//   cocg_update 3-term seed-COCG residual update with fused dots (Sec. II.B);
+//               cocg_update_df_kernel: the same on float hi + lo pairs (mixed
+//               and double-float modes; the double-float solve runs it only
+//               for its first step and in the relaxed phase, its other steps
+//               update inside the first H.V pass)
 //   cocg_seed   per-RHS seed scalars alpha_k, c_k and convergence test
 //   cocg_shift  per-shift recurrences pi, alpha^s, beta^s, projected p, G
 //   apply_op    S^gamma_q probe (Sec. V)
