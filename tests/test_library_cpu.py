@@ -8,6 +8,8 @@ import re
 import numpy as np
 import pytest
 
+from ftk_inputs import named
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -94,3 +96,13 @@ def test_suggest_order_rejects_bad_arguments(ftk):
         ftk.ftk_suggest_order(12, [(0, 12, 2)], ftk.FTK_FP64, 1)        # site out of range
     with pytest.raises(Exception):
         ftk.ftk_suggest_order(31, cl.bonds, ftk.FTK_FP64, 1)            # more sites than supported
+
+
+def test_no_fallback_without_the_library(ftk, monkeypatch):
+    """Without libftk.so every call raises (there is no CPU path)."""
+    monkeypatch.setattr(ftk, "_lib", None)
+    monkeypatch.setattr(ftk, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libftk.so"))
+    with pytest.raises(ftk.FtkError):
+        ftk.ftk_footprint(12, 1, 1, ftk.FTK_FP64)
+    with pytest.raises(ftk.FtkError):
+        ftk.ftk_suggest_order(12, named(12).bonds, ftk.FTK_FP64, 1)
