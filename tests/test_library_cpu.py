@@ -106,3 +106,21 @@ def test_no_fallback_without_the_library(ftk, monkeypatch):
         ftk.ftk_footprint(12, 1, 1, ftk.FTK_FP64)
     with pytest.raises(ftk.FtkError):
         ftk.ftk_suggest_order(12, named(12).bonds, ftk.FTK_FP64, 1)
+
+
+def test_product_and_oracle_are_independent():
+    """The product package (Python and CUDA sources) never imports or links the
+    oracle, and the oracle never imports the product; they share only the
+    seeded input generators (ftk_inputs)."""
+    pkg = os.path.join(ROOT, "paper_1802_02854_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
+                src = open(os.path.join(dirpath, f), encoding="utf-8").read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", src, re.M), f
+                assert "liboracle" not in src and "orc_" not in src, f
+    odir = os.path.join(ROOT, "oracle")
+    for f in os.listdir(odir):
+        if f.endswith((".py", ".c", ".h")):
+            src = open(os.path.join(odir, f), encoding="utf-8").read()
+            assert "paper_1802_02854_gb300" not in src and "ftk_" not in src.replace("ftk_inputs", ""), f
