@@ -18,6 +18,8 @@ Parts:
               Eq. B1 in M_d steps (Appendix A).
   filter.py   contour filter operators, equi-energy shells, their
               probability distribution and Green's function (Sec. II.C-D).
+  cocg3.py    shifted COCG in the three-term (residual-only) form of the
+              CUDA path, with optional seed switching.
 
 Every function is pinned by -m "not gpu" tests (tests/test_oracle_*.py)
 against closed forms, brute force, invariants and published test vectors.
