@@ -241,23 +241,27 @@ int64_t ftk_launch_count(const ftk_ctx *ctx);
 
 /* One mTPQ step that allocates no memory at all (no cudaMalloc/cudaFree, no
  * library allocator). The paper has no counterpart: this is a deployment
- * entry point for callers that cannot allocate device memory, e.g. while a
- * CUDA stream capture owned by someone else is open, inside allocation-free
- * real-time loops, or when all device memory belongs to a foreign pool. Such
- * callers cannot use ftk_create, which allocates small device buffers.
+ * entry point for callers that cannot allocate device memory, such as
+ * latency-bound loops that cannot afford the device-wide synchronisation an
+ * allocation may imply, or processes whose device memory is all held by a
+ * pool another framework owns (a cudaMalloc would fail there). Such callers
+ * cannot use ftk_create, which allocates small device buffers.
  *   out = (l - H/N) psi   (unnormalised; H as in ftk_create)
  * psi_dev, out_dev: caller-owned device vectors of 2^n_sites FP64 complex
  * amplitudes ((re, im) doubles), 16-byte aligned, not overlapping; psi must
  * be normalised. stats_out (host, 3 doubles) receives u = <psi|H|psi>/N,
  * <psi|H^2|psi> and q = ||out||, so out / q is the next mTPQ state.
- * Requires 2 <= n_sites <= FTK_NOALLOC_MAX_SITES and ell >= 0; other errors
- * as ftk_create (message via ftk_last_error(NULL)). Work runs on cuda_stream
- * (NULL = default stream); the call synchronises that stream.
+ * Requires 2 <= n_sites <= FTK_NOALLOC_MAX_SITES and, as ftk_tpq_init,
+ * ell >= l_min = (1/N) sum_b lambda_max(h_b); bonds as in ftk_create (else
+ * FTK_EINVAL, message via ftk_last_error(NULL)). Work runs on cuda_stream
+ * (NULL = the legacy default stream, which waits for every blocking stream);
+ * the call copies its three scalars to host memory and synchronises that
+ * stream before returning.
  * Scratch: a static device array of about 16 KB per GPU holds the reduction
  * partials of at most FTK_NOALLOC_MAX_GRID CTAs and the step's scalars; the
- * first call on a device looks up its address (make that first call before
- * any stream capture). All calls share it, so calls whose GPU work overlaps
- * (other threads or streams) race and must be serialised by the caller. */
+ * first call on a device looks up its address. All calls share it, so calls
+ * whose GPU work overlaps (other threads or streams) race and must be
+ * serialised by the caller. */
 #define FTK_NOALLOC_MAX_SITES 30
 #define FTK_NOALLOC_MAX_GRID 1024
 ftk_status ftk_tpq_step_noalloc(int32_t n_sites, const ftk_bond *bonds, int32_t n_bonds,

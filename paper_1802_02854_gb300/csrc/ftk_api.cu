@@ -467,9 +467,11 @@ ftk_status ftk_tpq_step(ftk_ctx *ctx, int32_t n_steps, int32_t save_every, doubl
     }
     CK(cudaStreamSynchronize(ctx->stream));
     if (n_steps > 0) {
-        if (u_out) CK(cudaMemcpy(u_out, stat_u(ctx) + k0, n_steps * sizeof(double), cudaMemcpyDeviceToHost));
-        if (logQ_out) CK(cudaMemcpy(logQ_out, stat_lq(ctx) + k0, n_steps * sizeof(double), cudaMemcpyDeviceToHost));
-        if (h2_out) CK(cudaMemcpy(h2_out, stat_h2(ctx) + k0, n_steps * sizeof(double), cudaMemcpyDeviceToHost));
+        if (u_out) CK(cudaMemcpyAsync(u_out, stat_u(ctx) + k0, n_steps * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        if (logQ_out)
+            CK(cudaMemcpyAsync(logQ_out, stat_lq(ctx) + k0, n_steps * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        if (h2_out) CK(cudaMemcpyAsync(h2_out, stat_h2(ctx) + k0, n_steps * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
     }
     return FTK_OK;
 }
@@ -483,7 +485,8 @@ ftk_status ftk_shells(const ftk_ctx *cctx, int32_t *n_out, int32_t *step_out, do
         if (step_out) step_out[s] = ctx->shell_step[s];
         if (energy_out) {
             double u = 0;
-            CK(cudaMemcpy(&u, stat_u(ctx) + ctx->shell_step[s], sizeof u, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpyAsync(&u, stat_u(ctx) + ctx->shell_step[s], sizeof u, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
             energy_out[s] = u * ctx->n;
         }
     }
@@ -623,7 +626,8 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     std::vector<double> e(n_rhs);
     CK(cudaStreamSynchronize(ctx->stream));
     for (int j = 0; j < n_rhs; ++j)
-        CK(cudaMemcpy(&e[j], ctx->slot_energy + slots[j], sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpyAsync(&e[j], ctx->slot_energy + slots[j], sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     const int mid = n_omega / 2;
     std::vector<CocgSeed> seeds(B);
     for (int j = 0; j < B; ++j) {
@@ -753,9 +757,10 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     CK(ce);
     // results
     std::vector<CocgSeed> out(B);
-    CK(cudaMemcpy(out.data(), d->seed, sizeof(CocgSeed) * B, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(out.data(), d->seed, sizeof(CocgSeed) * B, cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<double> g(2 * sa_elems);
-    CK(cudaMemcpy(g.data(), G, sa_elems * 16, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(g.data(), G, sa_elems * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     std::string why;
     for (int j = 0; j < n_rhs; ++j) {
         memcpy(G_out + size_t(2) * j * n_omega, g.data() + size_t(2) * j * n_omega, sizeof(double) * 2 * n_omega);
@@ -814,9 +819,10 @@ ftk_status ftk_spectrum(ftk_ctx *ctx, const double *Gh, int32_t n_shell, int32_t
     sp.trunc = trb;
     LAUNCH(launch_spectrum(sp, n_T, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    CK(cudaMemcpy(S_out, sb, sizeof(double) * n_T * n_omega, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(S_out, sb, sizeof(double) * n_T * n_omega, cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<int> tr(n_T);
-    CK(cudaMemcpy(tr.data(), trb, sizeof(int) * n_T, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(tr.data(), trb, sizeof(int) * n_T, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     int any = 0;
     for (int t = 0; t < n_T; ++t) {
         if (trunc_out) trunc_out[t] = tr[t];
@@ -861,7 +867,8 @@ ftk_status ftk_get_vector(ftk_ctx *ctx, int32_t which, double *host_out) {
     LAUNCH(launch_convert_out(which == 0 ? FTK_FP64 : ctx->vprec, src, stage, ctx->dim, scale,
                               vec_grid(ctx, ctx->dim), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    CK(cudaMemcpy(host_out, stage, ctx->dim * 16, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(host_out, stage, ctx->dim * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return FTK_OK;
 }
 

@@ -1,28 +1,29 @@
 // One mTPQ step through an entry point that allocates nothing.
 //
-// Who needs it: callers that must not allocate device memory, for example
-// code running while another library holds a CUDA stream capture open
-// (cudaMalloc is not allowed then), allocation-free real-time loops, or
-// hosts whose device memory is fully handed to a pool they do not own. Such a
-// caller cannot create an ftk_ctx (ftk_create allocates a few small device
-// buffers), so this entry point takes the Hamiltonian and two caller-owned
-// device vectors directly.
+// Who needs it: callers that must not allocate device memory. Examples are
+// latency-bound loops that cannot afford the device-wide synchronisation a
+// cudaMalloc or cudaFree may imply, and processes whose device memory has
+// been handed entirely to a pool that another framework owns, where a
+// cudaMalloc would fail. Such a caller cannot create an ftk_ctx (ftk_create
+// allocates a few small device buffers), so this entry point takes the
+// Hamiltonian and two caller-owned device vectors directly.
 //
 // Scratch: the per-CTA reduction partials, the last-CTA ticket, the reduced
 // dots and the step's scalars live in the file-scope array below (statically
 // sized; every GPU that loads the library holds it until the process exits).
 // Host code cannot use the array's name as a device address, so the first
 // call on each device looks the address up with cudaGetSymbolAddress (that
-// device current) and caches it; that first call should happen before any
-// stream capture. Every call shares the array and finds the previous call's
-// contents in it; the parts that must start at zero are cleared on the
-// stream first. Calls whose work overlaps on the GPU race on the array.
+// device current) and caches it. Every call shares the array and finds the
+// previous call's contents in it; the parts that must start at zero are
+// cleared on the stream first. Calls whose work overlaps on the GPU race on
+// the array.
 #include "../../include/ftk.h"
 #include "ftk_common.cuh"
 #include "ftk_kernels.h"
 #include "ftk_plan.h"
 
-#include <math.h>
+#include <algorithm>
+#include <cmath>
 
 using namespace ftk;
 
@@ -62,8 +63,15 @@ extern "C" ftk_status ftk_tpq_step_noalloc(int32_t n_sites, const ftk_bond *bond
     if (n_sites < 2 || n_sites > FTK_NOALLOC_MAX_SITES)
         return noalloc_fail(FTK_EINVAL, "ftk_tpq_step_noalloc: n_sites must be in [2, FTK_NOALLOC_MAX_SITES]");
     if (!bonds || n_bonds < 1 || n_bonds > 2 * FTK_MAX_PASS_BONDS || !psi_dev || !out_dev || !stats_out ||
-        psi_dev == out_dev || !(ell >= 0.0))
+        psi_dev == out_dev || !std::isfinite(K) || !std::isfinite(J) || !std::isfinite(ell))
         return noalloc_fail(FTK_EINVAL, "ftk_tpq_step_noalloc: bad arguments");
+    // the same rule as ftk_tpq_init: l >= l_min = (1/N) sum_b lambda_max(h_b),
+    // with the bond spectrum (J+K)/4 (twice), (J-K)/4, -(3J+K)/4, so that
+    // l - H/N is positive semidefinite (Appendix A)
+    const double lmax = std::max(std::max((J + K) / 4, (J - K) / 4), -(3 * J + K) / 4);
+    const double ell_min = n_bonds * lmax / n_sites;
+    if (!(ell >= ell_min - 1e-12))
+        return noalloc_fail(FTK_EINVAL, "ftk_tpq_step_noalloc: ell below l_min = (1/N) sum_b lambda_max(h_b)");
     if (((uintptr_t)psi_dev | (uintptr_t)out_dev) & 15)
         return noalloc_fail(FTK_EINVAL, "ftk_tpq_step_noalloc: vectors must be 16-byte aligned");
     PlanBond pb[2 * FTK_MAX_PASS_BONDS];

@@ -304,17 +304,24 @@ def test_pipeline_vs_dense_estimator(ftk, prec, eta):
 
 
 def test_fp32_small_eta_error_is_bounded(ftk):
-    """At eta = 0.02 the solves need ~2500 iterations and FP32 Krylov vectors
-    miss the 1e-5 bar: their rounding (6e-8 per step) accumulates through the
-    3-term recurrence, and some solves stagnate above the tolerance. The
-    error is recorded here (and by bench.py beside each FP32 number)."""
+    """At eta = 0.02 the solves need ~2500 iterations. FP32 Krylov vectors
+    miss the 1e-5 bar: each stored residual is rounded by 6e-8 of its norm,
+    and that perturbation reaches G amplified by 1/eta once per iteration
+    (the error grows with the sum of the shifted residuals, about
+    6e-8 / 0.02 * sum_k |r_k| / |pi_k|), and some solves stagnate above the
+    tolerance. Each FP32 spectrum is held to 5e-2. The mixed mode stores the
+    residuals as float pairs, so only the FP32 matvec error remains; its
+    spectra meet 1e-5 here (N = 12; at N = 24 the S^x spectra do not)."""
     for G, S, tr, ref, it in _pipeline(ftk, "fp32", 0.02, 1e-6):
         err = rel(S, ref["S"])
         print(f"fp32 eta=0.02 spectrum rel err {err:.3e}, iterations {it.tolist()}")
-    for G, S, tr, ref, it in _pipeline(ftk, "mixed", 0.02, 1e-6):
-        print(f"mixed eta=0.02 spectrum rel err {rel(S, ref['S']):.3e}, G err {rel(G.ravel(), ref['G'].ravel()):.3e}, "
-              f"iterations {it.tolist()}")
         assert err <= 5e-2
+        assert tr.tolist() == ref["trunc"].astype(int).tolist()
+    for G, S, tr, ref, it in _pipeline(ftk, "mixed", 0.02, 1e-6):
+        err = rel(S, ref["S"])
+        print(f"mixed eta=0.02 spectrum rel err {err:.3e}, G err {rel(G.ravel(), ref['G'].ravel()):.3e}, "
+              f"iterations {it.tolist()}")
+        assert err <= 1e-5
 
 
 @pytest.mark.parametrize("theta", [1e-2, 1e-3])

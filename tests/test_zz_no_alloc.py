@@ -1,11 +1,12 @@
 """The allocation-free mTPQ step (ftk_tpq_step_noalloc) against the regular
 context path (ftk_tpq_step), two calls in a row. GPU only.
 
-ftk_tpq_step_noalloc serves callers that cannot allocate device memory (an
-open stream capture owned by someone else, allocation-free loops, memory owned
-by a foreign pool); its reduction scratch is a static device array shared by
-all calls. This file is collected last so that a failure here leaves every
-other test already run."""
+ftk_tpq_step_noalloc serves callers that cannot allocate device memory
+(latency-bound loops that cannot take the synchronisation an allocation may
+imply, processes whose device memory belongs to another framework's pool);
+its reduction scratch is a static device array shared by all calls. This
+file is collected last so that a failure here leaves every other test
+already run."""
 import numpy as np
 import pytest
 
@@ -51,3 +52,23 @@ def test_noalloc_rejects_oversize():
         ftk.ftk_tpq_step_noalloc(31, cl.bonds, -1.0, 0.1, 0.5, 256, 512)
     assert e.value.status == ftk.FTK_EINVAL
     assert "FTK_NOALLOC_MAX_SITES" in str(e.value)
+
+
+def test_noalloc_rejects_small_ell():
+    """l below l_min = (1/N) sum_b lambda_max(h_b) is rejected as by
+    ftk_tpq_init (l - H/N would not be positive semidefinite)."""
+    import torch
+    from paper_1802_02854_gb300 import build
+    build.build()
+    import paper_1802_02854_gb300 as ftk
+
+    cl = named(8)
+    psi = torch.from_numpy(random_state(8, 3)).cuda()
+    out = torch.empty_like(psi)
+    # K = -1, J = 0.1: l_min = (3/2) (1 + J) / 4 = 0.4125
+    with pytest.raises(ftk.FtkError) as e:
+        ftk.ftk_tpq_step_noalloc(8, cl.bonds, -1.0, 0.1, 0.40, psi.data_ptr(), out.data_ptr())
+    assert e.value.status == ftk.FTK_EINVAL
+    assert "l_min" in str(e.value)
+    u, h2, q = ftk.ftk_tpq_step_noalloc(8, cl.bonds, -1.0, 0.1, 0.42, psi.data_ptr(), out.data_ptr())
+    assert q > 0
