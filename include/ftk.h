@@ -165,6 +165,103 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *rhs_slots, int32_t n_rh
                             double tol, int32_t max_iter,
                             double *G_out, int32_t *iters_out);
 
+/* Options of ftk_shifted_cocg_ex (a NULL pointer selects the defaults). */
+typedef struct {
+    /* Probe slots of the projection vectors, one per right-hand side: the
+     * solve then returns G^{AB}(z) = <lambda_A|(z - H)^{-1}|lambda_B> with
+     * lambda_B in rhs_slots[j] and lambda_A in proj_slots[j] (the A != B
+     * response of Sec. II.B, e.g. cross correlations of two operators).
+     * NULL: A = B. */
+    const int32_t *proj_slots;
+    /* Shift whose system is the initial seed; -1: n_shift / 2. */
+    int32_t seed_index;
+    /* 1: seed switching. When the seed system has converged while other
+     * shifts have not, the unconverged shift with the largest residual
+     * ||r_k|| / |pi^s_k| becomes the seed (the seed is moved as the
+     * truncation criterion of Appendix C follows the largest residual).
+     * Only residuals enter the recurrences, so the switch is an exact
+     * rescaling (r_k / pi*_k, r_{k-1} / pi*_{k-1}, pi / pi*): G and every
+     * shifted residual are unchanged, and a seed that converges early no
+     * longer drives its residual toward underflow. */
+    int32_t seed_switch;
+} ftk_cocg_opts;
+
+/* Shifted COCG as ftk_shifted_cocg with general complex shifts and the
+ * options above: G_j(s) = <lambda_{A,j}|(E_j + z_s - H)^{-1}|lambda_{B,j}>
+ * for shifts[2 s] + i shifts[2 s + 1] (host, [n_shift][2], imaginary parts
+ * > 0), E_j the shift origin of rhs slot j. switches_out (host [n_rhs], may
+ * be NULL) receives the number of seed switches per right-hand side. Other
+ * arguments, outputs, errors and synchronisation as ftk_shifted_cocg. */
+ftk_status ftk_shifted_cocg_ex(ftk_ctx *ctx, const int32_t *rhs_slots, int32_t n_rhs, const double *shifts,
+                               int32_t n_shift, double tol, int32_t max_iter, const ftk_cocg_opts *opts,
+                               double *G_out, int32_t *iters_out, int32_t *switches_out);
+
+/* Canonical TPQ states (Appendix A, Eq. B1) at the inverse temperatures
+ * beta[0..n_beta) (finite, >= 0, ascending):
+ *   |phi_b> = exp(N b (l - h)/2) |psi> / ||.||,   h = H / N,
+ * psi the current TPQ state (normalised), l the context's ell. Each
+ * increment db = beta[i] - beta[i-1] (beta[-1] = 0) is applied in M_d steps
+ * of the Taylor series of exp(tau (l - h)), tau = N db / (2 M_d), with M_d
+ * from the fixed point X of X_{j+1} = ln lam + ln(2 pi X_j) / 2 (X_0 = lam,
+ * so that the largest term of a step is about lam):
+ *   M_d = ceil(N db (l + |eps_0|) / (2 X)),  |eps_0| <= (1/N) sum_b |lambda_min(h_b)|;
+ * a step stops at the first term k >= X with X^k / k! <= 1e-17 (then the
+ * rest is below 1e-17 of the sum, l - h being positive semidefinite).
+ * Outputs (host, [n_beta], may be NULL): log ||exp(N b (l - h)/2) psi||,
+ * M_d of the increment, and the energy <phi_b|H|phi_b>. phi_b is kept as
+ * shell first_shell + i (scale 1; its shift origin is that energy), and the
+ * TPQ state becomes the last phi_b with the step counter reset to 0.
+ * Needs the Krylov region to hold two FP64 vectors (FTK_ENOMEM else) and
+ * first_shell + n_beta <= n_saved; lam > 1. Synchronises. */
+ftk_status ftk_ctpq(ftk_ctx *ctx, const double *beta, int32_t n_beta, double lam, int32_t first_shell,
+                    double *log_norm_out, int32_t *md_out, double *energy_out);
+
+/* Bytes of device scratch ftk_filter_shells needs for n_centres shells of
+ * n_points contour points each and at most max_iter Krylov iterations:
+ * 48 B per (iteration, contour point) of recorded shift recurrences plus
+ * 16 B per (iteration, shell) of coefficients. 0 on bad arguments
+ * (n_points <= 32, n_centres * n_points <= 4096). */
+size_t ftk_filter_footprint(int32_t n_centres, int32_t n_points, int32_t max_iter);
+
+/* Filtered typical states (Sec. II.C, Eq. dfilterP and Eq. filtered):
+ *   phi^m = P_{E_m, eps, M} phi
+ *         = (1/M) sum_{j=1..M} eps e^{i th_j} (eps e^{i th_j} + E_m - H)^{-1} phi,
+ *   th_j = 2 pi (j - 1/2) / M,  E_m = e_b + (2m + 1) eps,  m < n_centres,
+ * phi the normalised source: src = 0 the current TPQ state, src = 1 + s
+ * shell s (e.g. a cTPQ state from ftk_ctpq). All n_centres * M resolvents
+ * share phi, so one shifted COCG over all contour points runs twice: the
+ * first pass records the shift recurrences in scratch (caller-owned device
+ * memory of ftk_filter_footprint bytes, 256-byte aligned), the second
+ * replays the solve and accumulates each phi^m from the residuals with the
+ * coefficients of x^s = sum_k (T^s_k / pi^s_k) r_k. phi^m is written to
+ * shell first_shell + m (not normalised; its shift origin is E_m), probe
+ * slot 0 is overwritten (it holds phi). norm2_out (host [n_centres], may
+ * be NULL) receives <phi^m|phi^m>, iters_out (may be NULL) the iterations
+ * of one pass. The solve stops when every contour residual is below
+ * tol ||phi||. Needs precision FTK_FP64 and first_shell + n_centres <=
+ * n_saved. FTK_ENOCONV if max_iter is reached (no shells written).
+ * Synchronises. */
+ftk_status ftk_filter_shells(ftk_ctx *ctx, int32_t src, double e_b, double eps, int32_t n_centres,
+                             int32_t n_points, double tol, int32_t max_iter, void *scratch_dev,
+                             size_t scratch_bytes, int32_t first_shell, double *norm2_out,
+                             int32_t *iters_out);
+
+/* Reweighting of filter shells (Sec. II.D, Eqs. FRW1 and FRW2): with
+ * b' = 1 / T[t] and n_m = norm2[m] = <phi^m|phi^m> of shells built at
+ * inverse temperature beta,
+ *   S(omega, T) = sum_m e^{(b - b') E_m} S_m(omega) / sum_l e^{(b - b') E_l} n_l,
+ *   S_m(omega)  = -Im G_m(omega) / pi,
+ *   P_T(E_m)    = e^{(b - b') E_m} n_m / (2 eps sum_l e^{(b - b') E_l} n_l),
+ * G: host [n_shell][n_omega] complex (re, im), the Green's functions of the
+ * filtered shells (Eq. GAB_TPS: <phi^m|A^dag (omega + i eta + E_m - H)^{-1} A|phi^m>,
+ * e.g. ftk_apply_op on the shell then ftk_shifted_cocg); energy: host
+ * [n_shell] E_m. S_out: host [n_T][n_omega]; P_out: host [n_T][n_shell]
+ * (may be NULL). Computed on the device in double with log-sum-exp.
+ * Synchronises. */
+ftk_status ftk_filter_spectrum(ftk_ctx *ctx, const double *G, int32_t n_shell, int32_t n_omega,
+                               const double *energy, const double *norm2, double beta, double eps,
+                               const double *T, int32_t n_T, double *S_out, double *P_out);
+
 /* Temperature sweep by reweighting the saved shells (reading R1 of the
  * Taylor series Eq. B1; the shell-to-temperature map of Sec. III.D):
  *   S(omega, T) = sum_s W_s(1/T) S_s(omega) / sum_s W_s(1/T),

@@ -10,6 +10,10 @@ TEST INFRASTRUCTURE (see oracle/__init__.py): only tests/ use it.
     P(E_m) = <phi^m|phi^m> / (2 eps <phi_beta|phi_beta>)
     G^{AB}(zeta) = sum_m <phi^m| A^dag (zeta + E_m - H)^{-1} B |phi^m>
                    / <phi_beta|phi_beta>                          (Eq. GAB_TPS)
+    <O>_b' = sum_m e^{(b - b')E_m} <phi^m|O|phi^m>
+             / sum_l e^{(b - b')E_l} <phi^l|phi^l>                (Eq. FRW1)
+    P_b'(E_m) = e^{(b - b')E_m} <phi^m|phi^m>
+                / (2 eps sum_l e^{(b - b')E_l} <phi^l|phi^l>)     (Eq. FRW2)
 
 Every resolvent is applied by a textbook COCG solve of the complex-symmetric
 (z - H) x = b (H real symmetric), one shift at a time, with the oracle's
@@ -86,3 +90,20 @@ def green(cl, K, J, shells, phi_beta, e_b, eps, gamma_op, q, zetas, tol=1e-13):
         for i, zeta in enumerate(zetas):
             G[i] += np.vdot(lam, solve(cl, K, J, zeta + e, lam, tol))
     return G / nb
+
+
+def reweight(o_m, norm2, energies, beta, beta_p, eps):
+    """Eqs. FRW1 and FRW2: shells filtered at inverse temperature beta,
+    reweighted to beta_p. o_m: [L, ...] the shell expectation values
+    <phi^m|O|phi^m> (for a spectrum, -Im G_m(omega) / pi); norm2: [L]
+    <phi^m|phi^m>. Returns (<O>_beta_p [...], P_beta_p(E_m) [L]). Numerator
+    and denominator share the factor e^{-c}, c = max_m (beta - beta_p) E_m, so
+    no exponential overflows."""
+    o_m = np.asarray(o_m, dtype=np.float64)
+    n = np.asarray(norm2, dtype=np.float64)
+    E = np.asarray(energies, dtype=np.float64)
+    x = (beta - beta_p) * E
+    f = np.exp(x - x.max())
+    den = np.sum(f * n)
+    o = np.tensordot(f, o_m, axes=(0, 0)) / den
+    return o, f * n / (2.0 * eps * den)

@@ -29,7 +29,8 @@ STATUS_NAMES = ["FTK_OK", "FTK_EINVAL", "FTK_ENOMEM", "FTK_ECUDA", "FTK_ENOCONV"
 EXPORTS = ["ftk_footprint", "ftk_create", "ftk_bind_workspace", "ftk_tpq_init", "ftk_set_state",
            "ftk_tpq_step", "ftk_shells", "ftk_apply_op", "ftk_set_probe", "ftk_shifted_cocg",
            "ftk_spectrum", "ftk_hv", "ftk_get_vector", "ftk_plan_info", "ftk_launch_count",
-           "ftk_last_error", "ftk_destroy", "ftk_tpq_step_noalloc", "ftk_suggest_order", "ftk_autotune", "ftk_set_relax"]
+           "ftk_last_error", "ftk_destroy", "ftk_tpq_step_noalloc", "ftk_suggest_order", "ftk_autotune", "ftk_set_relax",
+           "ftk_shifted_cocg_ex", "ftk_ctpq", "ftk_filter_footprint", "ftk_filter_shells", "ftk_filter_spectrum"]
 
 
 class FtkError(RuntimeError):
@@ -50,6 +51,10 @@ class _Bond(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_rhs", C.c_int32), ("n_saved", C.c_int32),
                 ("tile_bits", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class _CocgOpts(C.Structure):
+    _fields_ = [("proj_slots", C.POINTER(C.c_int32)), ("seed_index", C.c_int32), ("seed_switch", C.c_int32)]
 
 
 _lib = None
@@ -91,8 +96,14 @@ def lib() -> C.CDLL:
     L.ftk_suggest_order.argtypes = [i32, C.POINTER(_Bond), i32, i32, i32, i32, pi, pi]
     L.ftk_autotune.argtypes = [vp, i32, i32, pi, pi, pd]
     L.ftk_set_relax.argtypes = [vp, C.c_double]
+    L.ftk_shifted_cocg_ex.argtypes = [vp, pi, i32, pd, i32, dbl, i32, C.POINTER(_CocgOpts), pd, pi, pi]
+    L.ftk_ctpq.argtypes = [vp, pd, i32, dbl, i32, pd, pi, pd]
+    L.ftk_filter_footprint.argtypes = [i32, i32, i32]
+    L.ftk_filter_footprint.restype = C.c_size_t
+    L.ftk_filter_shells.argtypes = [vp, i32, dbl, dbl, i32, i32, dbl, i32, vp, C.c_size_t, i32, pd, pi]
+    L.ftk_filter_spectrum.argtypes = [vp, pd, i32, i32, pd, pd, dbl, dbl, pd, i32, pd, pd]
     for name in EXPORTS:
-        if name not in ("ftk_footprint", "ftk_launch_count", "ftk_last_error", "ftk_destroy"):
+        if name not in ("ftk_footprint", "ftk_launch_count", "ftk_last_error", "ftk_destroy", "ftk_filter_footprint"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -189,6 +200,66 @@ def ftk_shifted_cocg(ctx, slots, omega, eta, tol, max_iter, allow_noconv=False):
     st = _check(ctx, lib().ftk_shifted_cocg(ctx, _ip(sl), len(sl), _dp(om), len(om), eta, tol, max_iter,
                                             G.ctypes.data_as(C.POINTER(C.c_double)), _ip(it)), ok)
     return G, it, st
+
+
+def ftk_shifted_cocg_ex(ctx, slots, shifts, tol, max_iter, proj_slots=None, seed_index=-1, seed_switch=False,
+                        allow_noconv=False):
+    """General complex shifts z_s = E_j + shifts[s] (Im > 0), optional
+    projection slots (A != B) and seed switching. Returns (G [n_rhs, n_shift],
+    iters [n_rhs], switches [n_rhs], status)."""
+    sl = np.ascontiguousarray(slots, dtype=np.int32)
+    z = np.ascontiguousarray(shifts, dtype=np.complex128)
+    G = np.zeros((len(sl), len(z)), dtype=np.complex128)
+    it = np.zeros(len(sl), dtype=np.int32)
+    sw = np.zeros(len(sl), dtype=np.int32)
+    pj = None if proj_slots is None else np.ascontiguousarray(proj_slots, dtype=np.int32)
+    opts = _CocgOpts(_ip(pj) if pj is not None else None, int(seed_index), 1 if seed_switch else 0)
+    ok = (FTK_OK, FTK_ENOCONV) if allow_noconv else (FTK_OK,)
+    st = _check(ctx, lib().ftk_shifted_cocg_ex(ctx, _ip(sl), len(sl), z.ctypes.data_as(C.POINTER(C.c_double)),
+                                               len(z), float(tol), int(max_iter), C.byref(opts),
+                                               G.ctypes.data_as(C.POINTER(C.c_double)), _ip(it), _ip(sw)), ok)
+    return G, it, sw, st
+
+
+def ftk_ctpq(ctx, betas, lam=1e4, first_shell=0):
+    """cTPQ states at the ascending betas (Appendix A), kept as shells
+    first_shell.. Returns (log norms, M_d per increment, energies)."""
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    ln = np.zeros(len(b))
+    md = np.zeros(len(b), dtype=np.int32)
+    en = np.zeros(len(b))
+    _check(ctx, lib().ftk_ctpq(ctx, _dp(b), len(b), float(lam), int(first_shell), _dp(ln), _ip(md), _dp(en)))
+    return ln, md, en
+
+
+def ftk_filter_footprint(n_centres, n_points, max_iter):
+    return int(lib().ftk_filter_footprint(int(n_centres), int(n_points), int(max_iter)))
+
+
+def ftk_filter_shells(ctx, src, e_b, eps, n_centres, n_points, tol, max_iter, scratch_ptr, scratch_bytes,
+                      first_shell=0):
+    """Filtered shells P_{E_m, eps, M} phi (Sec. II.C) into shells
+    first_shell..; returns (norms <phi^m|phi^m> [L], iterations)."""
+    n2 = np.zeros(int(n_centres))
+    it = C.c_int32()
+    _check(ctx, lib().ftk_filter_shells(ctx, int(src), float(e_b), float(eps), int(n_centres), int(n_points),
+                                        float(tol), int(max_iter), C.c_void_p(scratch_ptr), int(scratch_bytes),
+                                        int(first_shell), _dp(n2), C.byref(it)))
+    return n2, it.value
+
+
+def ftk_filter_spectrum(ctx, G, energy, norm2, beta, eps, T):
+    """Eqs. FRW1/FRW2: returns (S [n_T, n_omega], P [n_T, n_shell])."""
+    G = np.ascontiguousarray(G, dtype=np.complex128)
+    E = np.ascontiguousarray(energy, dtype=np.float64)
+    N2 = np.ascontiguousarray(norm2, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    S = np.zeros((len(T), G.shape[1]))
+    P = np.zeros((len(T), G.shape[0]))
+    _check(ctx, lib().ftk_filter_spectrum(ctx, G.ctypes.data_as(C.POINTER(C.c_double)), G.shape[0], G.shape[1],
+                                          _dp(E), _dp(N2), float(beta), float(eps), _dp(T), len(T), _dp(S),
+                                          _dp(P)))
+    return S, P
 
 
 def ftk_spectrum(ctx, G, T):
@@ -322,6 +393,33 @@ class Context:
 
     def spectrum(self, G, T):
         return ftk_spectrum(self.handle, G, T)
+
+    def shifted_cocg_ex(self, slots, shifts, tol=1e-4, max_iter=10000, proj_slots=None, seed_index=-1,
+                        seed_switch=False, allow_noconv=False):
+        return ftk_shifted_cocg_ex(self.handle, slots, shifts, tol, max_iter, proj_slots, seed_index, seed_switch,
+                                   allow_noconv)
+
+    def ctpq(self, betas, lam=1e4, first_shell=0):
+        return ftk_ctpq(self.handle, betas, lam, first_shell)
+
+    def filter_shells(self, src, e_b, eps, n_centres, n_points, tol=1e-10, max_iter=10000, first_shell=0):
+        """Filtered shells with a device scratch tensor of ftk_filter_footprint
+        bytes allocated (and released) here."""
+        torch = self.torch
+        nb = ftk_filter_footprint(n_centres, n_points, max_iter)
+        if nb == 0:
+            raise FtkError(FTK_EINVAL, "bad filter sizes")
+        scratch = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        torch.cuda.current_stream().synchronize()
+        try:
+            return ftk_filter_shells(self.handle, src, e_b, eps, n_centres, n_points, tol, max_iter,
+                                     scratch.data_ptr(), nb, first_shell)
+        finally:
+            self.stream.synchronize()
+            del scratch
+
+    def filter_spectrum(self, G, energy, norm2, beta, eps, T):
+        return ftk_filter_spectrum(self.handle, G, energy, norm2, beta, eps, T)
 
     def hv(self, v, out=None):
         """v: torch tensor [dim] or [B, dim] (B vectors, one after the other)

@@ -51,9 +51,9 @@ Layout make_layout(int n, int n_saved, int max_rhs, int prec) {
     if (prec == FTK_MIXED || prec == FTK_DF) off = align_up(off + (size_t(1) << n) * 16 * max_rhs);
     L.partials = off; off = align_up(off + kPartialsBytes);
     L.shift = off; off = align_up(off + size_t(kShiftArrays) * max_rhs * FTK_MAX_OMEGA * 16);
-    L.omega = off; off = align_up(off + FTK_MAX_OMEGA * 8);
+    L.omega = off; off = align_up(off + FTK_MAX_OMEGA * 16);   // complex shift offsets
     L.gbuf = off; off = align_up(off + size_t(1024) * FTK_MAX_OMEGA * 16);   // spectrum input G
-    L.tbuf = off; off = align_up(off + 1024 * 8);
+    L.tbuf = off; off = align_up(off + 3 * 1024 * 8);          // T; shell energies and norms
     L.total = off;
     return L;
 }
@@ -107,6 +107,10 @@ struct ftk_ctx {
     int k = 0, n_saved = 0, save_every = 1, have_state = 0;
     double ell = 0.5;
     std::vector<int> shell_step;
+    // shift origin of shells not produced by the mTPQ iteration (cTPQ and
+    // filtered shells); NaN: an mTPQ shell, origin N u_k from the statistics
+    std::vector<double> shell_origin;
+    cudaGraphExec_t cocg_exec = nullptr;   // instantiated COCG graph of the last solve
     std::vector<int> slot_valid;
     std::map<int, Plan> plans;       // by (precision, block width B): key prec * 64 + B
     int64_t launches = 0;
@@ -246,6 +250,13 @@ ftk_status check_ready(ftk_ctx *ctx) {
     if (!ctx) return FTK_EINVAL;
     if (!ctx->ws) return fail(ctx, FTK_ENOMEM, "no workspace bound");
     return FTK_OK;
+}
+
+// A shell slot below n_saved that holds a state: an mTPQ shell (step >= 0)
+// or a cTPQ / filtered shell (its origin set). Slots skipped by a
+// first_shell > n_saved are not written.
+bool shell_written(const ftk_ctx *ctx, int s) {
+    return s >= 0 && s < ctx->n_saved && (ctx->shell_step[s] >= 0 || !std::isnan(ctx->shell_origin[s]));
 }
 
 ftk_status check_ell(ftk_ctx *ctx, double ell) {
@@ -460,6 +471,8 @@ ftk_status ftk_tpq_step(ftk_ctx *ctx, int32_t n_steps, int32_t save_every, doubl
                                cudaMemcpyDeviceToDevice, ctx->stream));
             ctx->shell_step.resize(sidx + 1);
             ctx->shell_step[sidx] = k;
+            ctx->shell_origin.resize(sidx + 1);
+            ctx->shell_origin[sidx] = NAN;
             ctx->n_saved = sidx + 1;
         }
         if ((s = run_hv(ctx, FTK_FP64, 1, EPI_TPQ, cur, nxt, ea))) return s;
@@ -483,7 +496,11 @@ ftk_status ftk_shells(const ftk_ctx *cctx, int32_t *n_out, int32_t *step_out, do
     CK(cudaStreamSynchronize(ctx->stream));
     for (int s = 0; s < ctx->n_saved; ++s) {
         if (step_out) step_out[s] = ctx->shell_step[s];
-        if (energy_out) {
+        if (energy_out && !std::isnan(ctx->shell_origin[s])) {
+            energy_out[s] = ctx->shell_origin[s];   // cTPQ or filtered shell: its origin
+        } else if (energy_out && !shell_written(ctx, s)) {
+            energy_out[s] = NAN;                    // slot not written
+        } else if (energy_out) {
             double u = 0;
             CK(cudaMemcpyAsync(&u, stat_u(ctx) + ctx->shell_step[s], sizeof u, cudaMemcpyDeviceToHost, ctx->stream));
             CK(cudaStreamSynchronize(ctx->stream));
@@ -496,10 +513,11 @@ ftk_status ftk_shells(const ftk_ctx *cctx, int32_t *n_out, int32_t *step_out, do
 ftk_status ftk_apply_op(ftk_ctx *ctx, int32_t shell, int32_t gamma, const double q[2], int32_t slot) {
     ftk_status s = check_ready(ctx);
     if (s) return s;
-    if (shell < 0 || shell >= ctx->n_saved) return fail(ctx, FTK_EINVAL, "shell index out of range");
+    if (!shell_written(ctx, shell)) return fail(ctx, FTK_EINVAL, "shell index out of range or not written");
     if (gamma < 0 || gamma > 2 || !q) return fail(ctx, FTK_EINVAL, "bad gamma or q");
     if (slot < 0 || slot >= ctx->max_rhs) return fail(ctx, FTK_EINVAL, "rhs slot out of range");
-    if (ctx->shell_step[shell] >= ctx->k)
+    const bool tpq_shell = std::isnan(ctx->shell_origin[shell]);
+    if (tpq_shell && ctx->shell_step[shell] >= ctx->k)
         return fail(ctx, FTK_EBUSY, "shell statistics not computed yet (run one more TPQ step)");
     OpArgs oa{};
     oa.n_sites = ctx->n;
@@ -515,7 +533,8 @@ ftk_status ftk_apply_op(ftk_ctx *ctx, int32_t shell, int32_t gamma, const double
     oa.partials = (double *)wsp(ctx, ctx->L.partials);
     oa.counter = &ctx->dsmall->counters[2];
     oa.result = ctx->dsmall->op_dots;
-    oa.energy_src = stat_u(ctx) + ctx->shell_step[shell];
+    oa.energy_src = tpq_shell ? stat_u(ctx) + ctx->shell_step[shell] : nullptr;
+    oa.energy_val = tpq_shell ? 0.0 : ctx->shell_origin[shell];
     oa.n_sites_d = ctx->n;
     oa.slot_energy = ctx->slot_energy + slot;
     oa.slot_norm2 = ctx->slot_norm2 + slot;
@@ -547,9 +566,27 @@ ftk_status ftk_set_probe(ftk_ctx *ctx, int32_t slot, const double *v, int32_t is
 // elements later).
 static int upd_kind(const ftk_ctx *ctx) { return ctx->prec >= FTK_MIXED ? 2 : ctx->vprec; }
 
+// Extra launches of one COCG iteration beyond the standard ones: the seed
+// switch kernel (after the seed kernel) and the second-pass filter
+// accumulation (after the shift kernel, before the update).
+struct IterExtras {
+    const SwitchArgs *sw;        // NULL: no seed switching
+    const FilterAccArgs *acc;    // NULL: no accumulation
+};
+
 static ftk_status cocg_iteration(ftk_ctx *ctx, int B, void *rcur, void *rprev, void *w,
                                  EpiArgs ea, const SeedArgs &sa, const ShiftArgs &sh,
-                                 UpdArgs ua) {
+                                 UpdArgs ua, const IterExtras &ex) {
+    auto after_seed = [&](void *rc, void *rp) -> ftk_status {
+        if (ex.sw) {
+            SwitchArgs a = *ex.sw;
+            a.rcur = rc;
+            a.rprev = rp;
+            a.w = w;
+            LAUNCH(launch_cocg_switch(a, B, vec_grid(ctx, ctx->dim), ctx->stream));
+        }
+        return FTK_OK;
+    };
     if (ctx->prec == FTK_DF) {
         // double-float: the update r_{k-1} <- r_{k+1} of the previous step runs
         // inside the first pass of H r_{k+1} (rcur = r_k, rprev = r_{k-1})
@@ -582,67 +619,109 @@ static ftk_status cocg_iteration(ftk_ctx *ctx, int B, void *rcur, void *rprev, v
         ftk_status s = run_hv(ctx, ctx->mprec, B, EPI_COCG, rprev, w, ea);
         if (s) return s;
         LAUNCH(launch_cocg_seed(sa, ctx->stream));
+        // the new r_k is the buffer rprev (written by the fused update), r_{k-1} is rcur
+        if ((s = after_seed(rprev, rcur))) return s;
         LAUNCH(launch_cocg_shift(sh, B, ctx->stream));
         return FTK_OK;
     }
     if (ctx->prec == FTK_MIXED) ea.lo = static_cast<const char *>(rcur) + size_t(8) * ua.lo_stride;
-    if (ctx->prec == FTK_DF) ea.df_lo = ua.lo_stride;   // r and w: lo arrays one region half later
     ftk_status s = run_hv(ctx, ctx->mprec, B, EPI_COCG, rcur, w, ea);
     if (s) return s;
     LAUNCH(launch_cocg_seed(sa, ctx->stream));
+    if ((s = after_seed(rcur, rprev))) return s;
     LAUNCH(launch_cocg_shift(sh, B, ctx->stream));
+    if (ex.acc) {
+        FilterAccArgs a = *ex.acc;
+        a.r = static_cast<const double2 *>(rcur);
+        LAUNCH(launch_filter_acc(a, vec_grid(ctx, ctx->dim), ctx->stream));
+    }
     ua.mode = 1;
     LAUNCH(launch_cocg_update(upd_kind(ctx), B, rcur, w, rprev, ua, vec_grid(ctx, ctx->dim), ctx->stream));
     return FTK_OK;
 }
 
-ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, const double *omega,
-                            int32_t n_omega, double eta, double tol, int32_t max_iter, double *G_out,
-                            int32_t *iters_out) {
-    ftk_status s = check_ready(ctx);
-    if (s) return s;
-    if (!slots || n_rhs < 1 || n_rhs > ctx->max_rhs || !omega || n_omega < 1 || n_omega > FTK_MAX_OMEGA ||
-        !G_out || !(eta > 0) || !(tol > 0) || max_iter < 1)
-        return fail(ctx, FTK_EINVAL, "bad shifted COCG arguments");
-    for (int j = 0; j < n_rhs; ++j)
-        if (slots[j] < 0 || slots[j] >= ctx->max_rhs || !ctx->slot_valid[slots[j]])
-            return fail(ctx, FTK_EINVAL, "rhs slot not loaded");
+// One shifted-COCG solve of a block (the core of ftk_shifted_cocg,
+// ftk_shifted_cocg_ex and the contour filter).
+struct CocgReq {
+    const int32_t *slots = nullptr;     // probe slots of the right-hand sides
+    const int32_t *proj = nullptr;      // probe slots of the projection vectors (NULL: the rhs)
+    int n_rhs = 0;
+    const double *shift = nullptr;      // host [n_shift][2]: z_js - E_j
+    int n_shift = 0;
+    int seed_index = -1;                // -1: n_shift / 2
+    int seed_switch = 0;
+    double tol = 0;
+    int max_iter = 0;
+    dcx *hist = nullptr;                // device history (rhs 0), or NULL
+    int hist_cap = 0;
+    const FilterAccArgs *acc = nullptr; // second filter pass, or NULL
+};
+
+// Instantiated graph of the last solve; a later solve updates it in place
+// (cudaGraphExecUpdate) when the captured launch sequence has the same shape,
+// so repeated solves do not pay for a new instantiation.
+static ftk_status instantiate_cached(ftk_ctx *ctx, cudaGraph_t graph, cudaGraphExec_t *out) {
+    if (ctx->cocg_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(ctx->cocg_exec, graph, &info) == cudaSuccess) {
+            *out = ctx->cocg_exec;
+            return FTK_OK;
+        }
+        (void)cudaGetLastError();   // a failed update leaves no sticky error
+        cudaGraphExecDestroy(ctx->cocg_exec);
+        ctx->cocg_exec = nullptr;
+    }
+    CK(cudaGraphInstantiate(&ctx->cocg_exec, graph, 0));
+    *out = ctx->cocg_exec;
+    return FTK_OK;
+}
+
+static ftk_status cocg_core(ftk_ctx *ctx, const CocgReq &rq, double *G_out, int32_t *iters_out,
+                            int32_t *switches_out) {
+    const int n_rhs = rq.n_rhs, n_omega = rq.n_shift;
     int B = 1;
     while (B < n_rhs) B <<= 1;
     if (B > ctx->max_rhs) {
         // block wider than the Krylov region: split into two halves
+        if (rq.hist || rq.acc) return fail(ctx, FTK_EINVAL, "filter solves take one right-hand side");
         const int h = n_rhs / 2;
-        ftk_status s1 = ftk_shifted_cocg(ctx, slots, h, omega, n_omega, eta, tol, max_iter, G_out, iters_out);
+        CocgReq a = rq, b = rq;
+        a.n_rhs = h;
+        b.n_rhs = n_rhs - h;
+        b.slots = rq.slots + h;
+        if (rq.proj) b.proj = rq.proj + h;
+        ftk_status s1 = cocg_core(ctx, a, G_out, iters_out, switches_out);
         if (s1 != FTK_OK && s1 != FTK_ENOCONV && s1 != FTK_EBREAKDOWN) return s1;
-        ftk_status s2 = ftk_shifted_cocg(ctx, slots + h, n_rhs - h, omega, n_omega, eta, tol, max_iter,
-                                         G_out + size_t(2) * h * n_omega, iters_out ? iters_out + h : nullptr);
+        ftk_status s2 = cocg_core(ctx, b, G_out + size_t(2) * h * n_omega, iters_out ? iters_out + h : nullptr,
+                                  switches_out ? switches_out + h : nullptr);
         if (s2 != FTK_OK && s2 != FTK_ENOCONV && s2 != FTK_EBREAKDOWN) return s2;
         return s1 != FTK_OK ? s1 : s2;
     }
+    ftk_status s;
     Plan *pl = nullptr;
     if ((s = get_plan(ctx, ctx->mprec, B, &pl))) return s;
     Small *d = ctx->dsmall;
-    // per-RHS seed scalars: z_s = E_j + omega[mid] + i eta
+    // per-RHS seed scalars: z_s = E_j + shift[seed]
     std::vector<double> e(n_rhs);
-    CK(cudaStreamSynchronize(ctx->stream));
     for (int j = 0; j < n_rhs; ++j)
-        CK(cudaMemcpyAsync(&e[j], ctx->slot_energy + slots[j], sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(&e[j], ctx->slot_energy + rq.slots[j], sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    const int mid = n_omega / 2;
+    const int mid = rq.seed_index >= 0 ? rq.seed_index : n_omega / 2;
     std::vector<CocgSeed> seeds(B);
     for (int j = 0; j < B; ++j) {
         memset(&seeds[j], 0, sizeof(CocgSeed));
         const int jj = j < n_rhs ? j : 0;          // padding lanes repeat RHS 0
         seeds[j].e0 = e[jj];
-        seeds[j].zs_re = e[jj] + omega[mid];
-        seeds[j].zs_im = eta;
+        seeds[j].zs_re = e[jj] + rq.shift[2 * mid];
+        seeds[j].zs_im = rq.shift[2 * mid + 1];
         seeds[j].alpha_re = 1.0;
+        seeds[j].seed_idx = mid;
     }
     CK(cudaMemcpyAsync(d->seed, seeds.data(), sizeof(CocgSeed) * B, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(d->inv_pi_max, 0, sizeof(d->inv_pi_max), ctx->stream));
     CK(cudaMemsetAsync(&d->all_done, 0, sizeof(int) * 2, ctx->stream));   // all_done, lowp
-    double *om = (double *)wsp(ctx, ctx->L.omega);
-    CK(cudaMemcpyAsync(om, omega, sizeof(double) * n_omega, cudaMemcpyHostToDevice, ctx->stream));
+    dcx *om = (dcx *)wsp(ctx, ctx->L.omega);
+    CK(cudaMemcpyAsync(om, rq.shift, sizeof(dcx) * n_omega, cudaMemcpyHostToDevice, ctx->stream));
     // shift arrays: pi_prev = pi_cur = 1, p~ = 0, G = 0
     const size_t sa_elems = size_t(B) * n_omega;
     dcx *sbase = (dcx *)wsp(ctx, ctx->L.shift);
@@ -662,7 +741,8 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     ua.dim = ctx->dim;
     for (int j = 0; j < B; ++j) {
         const int jj = j < n_rhs ? j : 0;
-        ua.lambda[j] = wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * slots[jj]);
+        ua.lambda[j] = wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * rq.slots[jj]);
+        ua.proj[j] = rq.proj ? wsp(ctx, ctx->L.probes + ctx->L.vec_bytes * rq.proj[jj]) : nullptr;
     }
     ua.seed = d->seed;
     ua.partials = (double *)wsp(ctx, ctx->L.partials);
@@ -679,8 +759,8 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     ea.all_done = &d->all_done;
     SeedArgs sa{};
     sa.n_rhs = B;
-    sa.max_iter = max_iter;
-    sa.tol = tol;
+    sa.max_iter = rq.max_iter;
+    sa.tol = rq.tol;
     sa.seed = d->seed;
     sa.upd = d->upd_dots;
     sa.hv = d->hv_dots;
@@ -688,15 +768,33 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     sa.all_done = &d->all_done;
     sa.relax = ctx->relax;
     sa.lowp = &d->lowp;
+    sa.seed_switch = rq.seed_switch;
+    sa.n_omega = n_omega;
+    sa.shift = om;
+    sa.pi_prev = pi_prev;
+    sa.pi_cur = pi_cur;
     ShiftArgs sh{};
     sh.n_omega = n_omega;
-    sh.seed_idx = mid;
-    sh.omega = om;
+    sh.shift = om;
     sh.seed = d->seed;
     sh.pi_prev = pi_prev; sh.pi_cur = pi_cur; sh.ptil = ptil; sh.G = G;
     sh.inv_pi_max = d->inv_pi_max;
     sh.frozen = reinterpret_cast<int *>(sbase + 4 * sa_elems);
-    sh.tol = tol;
+    sh.tol = rq.tol;
+    sh.hist = rq.hist;
+    sh.hist_cap = rq.hist_cap;
+    sa.frozen = sh.frozen;
+    SwitchArgs swa{};
+    swa.kind = upd_kind(ctx);
+    swa.dim = ctx->dim;
+    swa.lo_stride = ua.lo_stride;
+    swa.w_lo = ctx->prec == FTK_DF ? ua.lo_stride : 0;
+    swa.seed = d->seed;
+    swa.pi_prev = pi_prev;
+    swa.pi_cur = pi_cur;
+    swa.n_omega = n_omega;
+    swa.all_done = &d->all_done;
+    IterExtras ex{rq.seed_switch ? &swa : nullptr, rq.acc};
 
     // r_0 = lambda (+ dots); r_{-1} = 0 so that c_0 r_{-1} is exactly zero
     if (ctx->prec >= FTK_MIXED) {   // hi and lo parts of the B columns
@@ -727,22 +825,22 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     {
         std::lock_guard<std::mutex> lk(device_mu());
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        ftk_status cs = cocg_iteration(ctx, B, rcur, rprev, w, ea, sa, sh, ua);
-        if (cs == FTK_OK) cs = cocg_iteration(ctx, B, rprev, rcur, w, ea, sa, sh, ua);
+        ftk_status cs = cocg_iteration(ctx, B, rcur, rprev, w, ea, sa, sh, ua, ex);
+        if (cs == FTK_OK) cs = cocg_iteration(ctx, B, rprev, rcur, w, ea, sa, sh, ua, ex);
         ce = cudaStreamEndCapture(ctx->stream, &graph);
         if (cs != FTK_OK) { if (graph) cudaGraphDestroy(graph); return cs; }
         CK(ce);
         per_graph = ctx->launches - l0;
         ctx->launches = l0;
-        ce = cudaGraphInstantiate(&exec, graph, 0);
+        const ftk_status is = instantiate_cached(ctx, graph, &exec);
         cudaGraphDestroy(graph);
-        CK(ce);
+        if (is != FTK_OK) return is;
     }
     int done = 0, it = it0;
     const int chunk = 16;   // graph launches between host checks (32 iterations)
     ftk_status result = FTK_OK;
     while (!done) {
-        for (int g = 0; g < chunk && it <= max_iter + 2; ++g, it += 2) {
+        for (int g = 0; g < chunk && it <= rq.max_iter + 2; ++g, it += 2) {
             ce = cudaGraphLaunch(exec, ctx->stream);
             if (ce != cudaSuccess) break;
             ctx->launches += per_graph;
@@ -751,9 +849,8 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
         ce = cudaMemcpyAsync(&done, &d->all_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
         if (ce != cudaSuccess) break;
-        if (it > max_iter + 2) break;
+        if (it > rq.max_iter + 2) break;
     }
-    cudaGraphExecDestroy(exec);
     CK(ce);
     // results
     std::vector<CocgSeed> out(B);
@@ -763,8 +860,9 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     CK(cudaStreamSynchronize(ctx->stream));
     std::string why;
     for (int j = 0; j < n_rhs; ++j) {
-        memcpy(G_out + size_t(2) * j * n_omega, g.data() + size_t(2) * j * n_omega, sizeof(double) * 2 * n_omega);
+        if (G_out) memcpy(G_out + size_t(2) * j * n_omega, g.data() + size_t(2) * j * n_omega, sizeof(double) * 2 * n_omega);
         if (iters_out) iters_out[j] = out[j].iters;
+        if (switches_out) switches_out[j] = out[j].switches;
         const int dn = out[j].done;
         if ((dn == 2 || dn == 3 || dn == 5) && result != FTK_EBREAKDOWN) {
             result = FTK_EBREAKDOWN;
@@ -779,6 +877,384 @@ ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, c
     return result;
 }
 
+static ftk_status check_cocg_args(ftk_ctx *ctx, const int32_t *slots, const int32_t *proj, int32_t n_rhs,
+                                  int32_t n_shift, double tol, int32_t max_iter) {
+    if (!slots || n_rhs < 1 || n_rhs > FTK_MAX_RHS * 64 || n_shift < 1 || n_shift > FTK_MAX_OMEGA || !(tol > 0) ||
+        max_iter < 1)
+        return fail(ctx, FTK_EINVAL, "bad shifted COCG arguments");
+    for (int j = 0; j < n_rhs; ++j) {
+        if (slots[j] < 0 || slots[j] >= ctx->max_rhs || !ctx->slot_valid[slots[j]])
+            return fail(ctx, FTK_EINVAL, "rhs slot not loaded");
+        if (proj && (proj[j] < 0 || proj[j] >= ctx->max_rhs || !ctx->slot_valid[proj[j]]))
+            return fail(ctx, FTK_EINVAL, "projection slot not loaded");
+    }
+    return FTK_OK;
+}
+
+ftk_status ftk_shifted_cocg(ftk_ctx *ctx, const int32_t *slots, int32_t n_rhs, const double *omega,
+                            int32_t n_omega, double eta, double tol, int32_t max_iter, double *G_out,
+                            int32_t *iters_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (!omega || !G_out || !(eta > 0) || n_rhs > ctx->max_rhs)
+        return fail(ctx, FTK_EINVAL, "bad shifted COCG arguments");
+    if ((s = check_cocg_args(ctx, slots, nullptr, n_rhs, n_omega, tol, max_iter))) return s;
+    std::vector<double> z(2 * size_t(n_omega));
+    for (int i = 0; i < n_omega; ++i) { z[2 * i] = omega[i]; z[2 * i + 1] = eta; }
+    CocgReq rq;
+    rq.slots = slots;
+    rq.n_rhs = n_rhs;
+    rq.shift = z.data();
+    rq.n_shift = n_omega;
+    rq.tol = tol;
+    rq.max_iter = max_iter;
+    return cocg_core(ctx, rq, G_out, iters_out, nullptr);
+}
+
+ftk_status ftk_shifted_cocg_ex(ftk_ctx *ctx, const int32_t *rhs_slots, int32_t n_rhs, const double *shifts,
+                               int32_t n_shift, double tol, int32_t max_iter, const ftk_cocg_opts *opts,
+                               double *G_out, int32_t *iters_out, int32_t *switches_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    const int32_t *proj = opts ? opts->proj_slots : nullptr;
+    if (!shifts || !G_out || n_rhs > ctx->max_rhs) return fail(ctx, FTK_EINVAL, "bad shifted COCG arguments");
+    if ((s = check_cocg_args(ctx, rhs_slots, proj, n_rhs, n_shift, tol, max_iter))) return s;
+    for (int i = 0; i < n_shift; ++i)
+        if (!std::isfinite(shifts[2 * i]) || !(shifts[2 * i + 1] > 0))
+            return fail(ctx, FTK_EINVAL, "shifts must be finite with positive imaginary part");
+    CocgReq rq;
+    rq.slots = rhs_slots;
+    rq.proj = proj;
+    rq.n_rhs = n_rhs;
+    rq.shift = shifts;
+    rq.n_shift = n_shift;
+    rq.tol = tol;
+    rq.max_iter = max_iter;
+    if (opts) {
+        if (opts->seed_index < -1 || opts->seed_index >= n_shift)
+            return fail(ctx, FTK_EINVAL, "seed_index out of range");
+        rq.seed_index = opts->seed_index;
+        rq.seed_switch = opts->seed_switch ? 1 : 0;
+    }
+    return cocg_core(ctx, rq, G_out, iters_out, switches_out);
+}
+
+// ---------------------------------------------------------------- cTPQ (f2)
+// Appendix A: exp(N b (l - h)/2) psi applied as M_d Taylor steps of
+// tau = N db / (2 M_d) for each increment db of the (ascending) beta list.
+// The step count comes from the fixed point of X_{j+1} = ln Lambda + ln(2 pi X_j)/2
+// (the largest term X^k/k! of a step is then about Lambda), X_0 = Lambda,
+// M_d = ceil(N db (l + |eps_0|) / (2 X)). |eps_0| is bounded by the bond
+// spectrum: (1/N) sum_b |lambda_min(h_b)|. One step sums
+// t_0 = v, t_{k+1} = tau/(k+1) (l - h) t_k up to the first k >= X with
+// X^k / k! <= 1e-17: since l - h is positive semidefinite the sum is at least
+// |v|, and |t_k| <= X^k/k! |v|, so the dropped tail is below 1e-17 of it.
+static int ctpq_steps(int n, double dbeta, double ell, double eps0, double lam, double *x_out) {
+    double x = lam;
+    for (int i = 0; i < 1000; ++i) {
+        const double nx = std::log(lam) + 0.5 * std::log(2.0 * M_PI * x);
+        const bool fin = std::fabs(nx - x) <= 1e-15 * std::fabs(nx);
+        x = nx;
+        if (fin) break;
+    }
+    *x_out = x;
+    const double md = std::ceil(n * dbeta / 2.0 * (ell + eps0) / x);
+    return std::max(1, (int)md);
+}
+
+static int taylor_terms(double X) {
+    int k = 1;
+    while (k < 100000) {
+        if (k >= X && k * std::log(std::max(X, 1e-300)) - std::lgamma(k + 1.0) <= std::log(1e-17)) break;
+        ++k;
+    }
+    return k;
+}
+
+ftk_status ftk_ctpq(ftk_ctx *ctx, const double *beta, int32_t n_beta, double lam, int32_t first_shell,
+                    double *log_norm_out, int32_t *md_out, double *energy_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (!ctx->have_state) return fail(ctx, FTK_EBUSY, "no TPQ state: call ftk_tpq_init first");
+    if (!beta || n_beta < 1 || !(lam > 1.0) || first_shell < 0 || first_shell + n_beta > ctx->n_saved_cap)
+        return fail(ctx, FTK_EINVAL, "ftk_ctpq: bad arguments (beta list, Lambda > 1, shells within n_saved)");
+    for (int i = 0; i < n_beta; ++i)
+        if (!(beta[i] >= 0.0) || !std::isfinite(beta[i]) || (i > 0 && beta[i] < beta[i - 1]))
+            return fail(ctx, FTK_EINVAL, "ftk_ctpq: betas must be finite, >= 0 and ascending");
+    if (ctx->L.vec_bytes * 3 * (size_t)ctx->max_rhs < ctx->dim * 32)
+        return fail(ctx, FTK_ENOMEM, "ftk_ctpq: the Krylov region must hold two FP64 vectors");
+    Plan *pl64 = nullptr;
+    if ((s = get_plan(ctx, FTK_FP64, 1, &pl64))) return s;
+    const double lmin = std::min({(ctx->J + ctx->K) / 4, (ctx->J - ctx->K) / 4, -(3 * ctx->J + ctx->K) / 4});
+    const double eps0 = ctx->nb * std::fabs(lmin) / ctx->n;
+    // buffers: V = psi[0] (the state), C = psi[1] (the step's sum), terms in the Krylov region
+    double2 *V = (double2 *)wsp(ctx, ctx->L.psi[0]);
+    double2 *C = (double2 *)wsp(ctx, ctx->L.psi[1]);
+    double2 *T0 = (double2 *)wsp(ctx, ctx->L.kry[0]);
+    double2 *T1 = T0 + ctx->dim;
+    double *dscale = &ctx->dsmall->op_dots[3];
+    // the current state, normalised, into V (through T0 when it already is V)
+    const void *cur = wsp(ctx, ctx->L.psi[ctx->k & 1]);
+    LAUNCH(launch_convert_out(FTK_FP64, cur, T0, ctx->dim, &ctx->dsmall->tpq.scale, vec_grid(ctx, ctx->dim),
+                              ctx->stream));
+    CK(cudaMemcpyAsync(V, T0, ctx->dim * 16, cudaMemcpyDeviceToDevice, ctx->stream));
+    EpiArgs ea{};
+    ea.ell = ctx->ell;
+    ea.inv_n = 1.0 / ctx->n;
+    ea.partials = (double *)wsp(ctx, ctx->L.partials);
+    ea.counter = &ctx->dsmall->counters[1];
+    ea.result = ctx->dsmall->op_dots;
+    ea.taylor_acc = C;
+    double log_norm = 0.0, prev = 0.0;
+    for (int i = 0; i < n_beta; ++i) {
+        const double db = beta[i] - prev;
+        prev = beta[i];
+        int md = 0;
+        if (db > 0.0) {
+            double X = 0;
+            md = ctpq_steps(ctx->n, db, ctx->ell, eps0, lam, &X);
+            const double tau = ctx->n * db / (2.0 * md);
+            const int kmax = taylor_terms(tau * (ctx->ell + eps0));
+            for (int st = 0; st < md; ++st) {
+                CK(cudaMemcpyAsync(C, V, ctx->dim * 16, cudaMemcpyDeviceToDevice, ctx->stream));
+                const double2 *in = V;
+                for (int k = 0; k < kmax; ++k) {
+                    double2 *out = (k & 1) ? T1 : T0;
+                    EpiArgs e = ea;
+                    e.tcoef = tau / (k + 1);
+                    if ((s = run_hv(ctx, FTK_FP64, 1, EPI_TAYLOR, in, out, e))) return s;
+                    in = out;
+                }
+                // V = C / |C|, log |C| accumulated
+                double n2 = 0;
+                CK(cudaMemcpyAsync(&n2, ctx->dsmall->op_dots + 1, sizeof n2, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+                if (!(n2 > 0) || !std::isfinite(n2)) return fail(ctx, FTK_EBREAKDOWN, "ftk_ctpq: non-finite Taylor sum");
+                log_norm += 0.5 * std::log(n2);
+                const double sc = 1.0 / std::sqrt(n2);
+                CK(cudaMemcpyAsync(dscale, &sc, sizeof sc, cudaMemcpyHostToDevice, ctx->stream));
+                LAUNCH(launch_convert_out(FTK_FP64, C, V, ctx->dim, dscale, vec_grid(ctx, ctx->dim), ctx->stream));
+            }
+        }
+        // energy <phi|H|phi> of the normalised state: one Taylor pass with c = 0
+        CK(cudaMemcpyAsync(C, V, ctx->dim * 16, cudaMemcpyDeviceToDevice, ctx->stream));
+        EpiArgs e = ea;
+        e.tcoef = 0.0;
+        if ((s = run_hv(ctx, FTK_FP64, 1, EPI_TAYLOR, V, T0, e))) return s;
+        double en = 0;
+        CK(cudaMemcpyAsync(&en, ctx->dsmall->op_dots, sizeof en, cudaMemcpyDeviceToHost, ctx->stream));
+        // the state into its shell (context vector precision), scale 1, origin its energy
+        const int sidx = first_shell + i;
+        void *dst = wsp(ctx, ctx->L.shells + ctx->L.vec_bytes * sidx);
+        if (ctx->vprec == 0)
+            CK(cudaMemcpyAsync(dst, V, ctx->L.vec_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        else
+            LAUNCH(launch_convert_in(ctx->vprec, V, dst, ctx->dim, vec_grid(ctx, ctx->dim), ctx->stream));
+        const double one = 1.0;
+        CK(cudaMemcpyAsync(ctx->shell_scale + sidx, &one, sizeof one, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if ((int)ctx->shell_step.size() <= sidx) {
+            ctx->shell_step.resize(sidx + 1, -1);
+            ctx->shell_origin.resize(sidx + 1, NAN);
+        }
+        ctx->shell_step[sidx] = -1;
+        ctx->shell_origin[sidx] = en;
+        ctx->n_saved = std::max(ctx->n_saved, sidx + 1);
+        if (log_norm_out) log_norm_out[i] = log_norm;
+        if (md_out) md_out[i] = md;
+        if (energy_out) energy_out[i] = en;
+    }
+    // the TPQ state becomes the last cTPQ state (normalised, step counter 0)
+    TpqState h{};
+    h.scale = 1.0;
+    h.ell = ctx->ell;
+    h.n_sites = ctx->n;
+    CK(cudaMemcpyAsync(&ctx->dsmall->tpq, &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->k = 0;
+    return FTK_OK;
+}
+
+// ------------------------------------------------------ filter shells (f1)
+// Eq. dfilterP / Eq. filtered: phi^m = (1/M) sum_j rho e^{i th_j} (E_m + rho e^{i th_j} - H)^{-1} phi,
+// th_j = 2 pi (j - 1/2) / M, E_m = E_b + (2m + 1) eps, rho = eps. All L M
+// resolvents share the right-hand side phi, so ONE shifted COCG over the L M
+// contour points serves every shell. The solution vectors are not kept per
+// shift: pass 1 runs the solve and records the shift recurrences; from them
+// x^s = sum_k C^s_k r_k (backward sums); pass 2 replays the same solve
+// (deterministic reductions: the same r_k) and accumulates
+// phi^m += sum_j w_j C^{(m, j)}_k r_k into L vectors.
+static size_t filter_hist_bytes(int L, int M, int max_iter) { return align_up(size_t(48) * L * M * max_iter); }
+static size_t filter_coef_bytes(int L, int max_iter) { return align_up(size_t(16) * L * max_iter); }
+
+size_t ftk_filter_footprint(int32_t n_centres, int32_t n_points, int32_t max_iter) {
+    if (n_centres < 1 || n_points < 1 || n_points > 32 || (size_t)n_centres * n_points > FTK_MAX_OMEGA ||
+        max_iter < 1)
+        return 0;
+    return filter_hist_bytes(n_centres, n_points, max_iter) + filter_coef_bytes(n_centres, max_iter) +
+           align_up(size_t(16) * n_points);
+}
+
+ftk_status ftk_filter_shells(ftk_ctx *ctx, int32_t src, double e_b, double eps, int32_t n_centres, int32_t n_points,
+                             double tol, int32_t max_iter, void *scratch, size_t scratch_bytes, int32_t first_shell,
+                             double *norm2_out, int32_t *iters_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    const int L = n_centres, M = n_points;
+    if (ctx->prec != FTK_FP64) return fail(ctx, FTK_EINVAL, "ftk_filter_shells: needs precision FTK_FP64");
+    const size_t need = ftk_filter_footprint(L, M, max_iter);
+    if (need == 0 || !std::isfinite(e_b) || !(eps > 0) || !(tol > 0) || first_shell < 0 ||
+        first_shell + L > ctx->n_saved_cap)
+        return fail(ctx, FTK_EINVAL, "ftk_filter_shells: bad arguments (M <= 32, L M <= 4096, shells within n_saved)");
+    if (!scratch || scratch_bytes < need || (reinterpret_cast<uintptr_t>(scratch) % kAlign))
+        return fail(ctx, FTK_ENOMEM, "ftk_filter_shells: scratch missing, unaligned or smaller than ftk_filter_footprint");
+    // source phi (normalised) into probe slot 0, shift origin 0
+    const void *sv = nullptr;
+    const double *scale = nullptr;
+    if (src == 0) {
+        if (!ctx->have_state) return fail(ctx, FTK_EBUSY, "no TPQ state");
+        sv = wsp(ctx, ctx->L.psi[ctx->k & 1]);
+        scale = &ctx->dsmall->tpq.scale;
+    } else {
+        const int sh = src - 1;
+        if (!shell_written(ctx, sh)) return fail(ctx, FTK_EINVAL, "ftk_filter_shells: no such source shell");
+        if (sh >= first_shell && sh < first_shell + L)
+            return fail(ctx, FTK_EINVAL, "ftk_filter_shells: the source shell would be overwritten");
+        sv = wsp(ctx, ctx->L.shells + ctx->L.vec_bytes * sh);
+        scale = ctx->shell_scale + sh;
+    }
+    double2 *lam = (double2 *)wsp(ctx, ctx->L.probes);
+    LAUNCH(launch_convert_out(FTK_FP64, sv, lam, ctx->dim, scale, vec_grid(ctx, ctx->dim), ctx->stream));
+    const double zero = 0.0;
+    CK(cudaMemcpyAsync(ctx->slot_energy, &zero, sizeof zero, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->slot_valid[0] = 1;
+    // contour points z = E_m + eps e^{i th_j} (shift s = m M + j) and weights
+    std::vector<double> z(2 * size_t(L) * M);
+    std::vector<dcx> w(M);
+    for (int j = 0; j < M; ++j) {
+        const double th = 2.0 * M_PI * (j + 0.5) / M;
+        w[j] = {eps * std::cos(th) / M, eps * std::sin(th) / M};
+        for (int m = 0; m < L; ++m) {
+            const double em = e_b + (2 * m + 1) * eps;
+            z[2 * (size_t(m) * M + j)] = em + eps * std::cos(th);
+            z[2 * (size_t(m) * M + j) + 1] = eps * std::sin(th);
+        }
+    }
+    char *scr = static_cast<char *>(scratch);
+    dcx *hist = reinterpret_cast<dcx *>(scr);
+    dcx *coef = reinterpret_cast<dcx *>(scr + filter_hist_bytes(L, M, max_iter));
+    dcx *wdev = reinterpret_cast<dcx *>(scr + filter_hist_bytes(L, M, max_iter) + filter_coef_bytes(L, max_iter));
+    CK(cudaMemcpyAsync(wdev, w.data(), sizeof(dcx) * M, cudaMemcpyHostToDevice, ctx->stream));
+    const int32_t slot0 = 0;
+    CocgReq rq;
+    rq.slots = &slot0;
+    rq.n_rhs = 1;
+    rq.shift = z.data();
+    rq.n_shift = L * M;
+    rq.seed_index = (L / 2) * M;   // th = pi / M: the smallest positive imaginary part
+    rq.tol = tol;
+    rq.max_iter = max_iter;
+    rq.hist = hist;
+    rq.hist_cap = max_iter;
+    int32_t it1 = 0, it2 = 0;
+    s = cocg_core(ctx, rq, nullptr, &it1, nullptr);
+    if (s != FTK_OK) return s;
+    FilterCoefArgs fc{};
+    fc.n_iter = it1;
+    fc.L = L;
+    fc.M = M;
+    fc.hist = hist;
+    fc.w = wdev;
+    fc.coef = coef;
+    LAUNCH(launch_filter_coef(fc, ctx->stream));
+    double2 *phi = (double2 *)wsp(ctx, ctx->L.shells + ctx->L.vec_bytes * first_shell);
+    CK(cudaMemsetAsync(phi, 0, ctx->L.vec_bytes * L, ctx->stream));
+    FilterAccArgs fa{};
+    fa.dim = ctx->dim;
+    fa.L = L;
+    fa.n_coef = it1;
+    fa.phi = phi;
+    fa.coef = coef;
+    fa.seed = ctx->dsmall->seed;
+    rq.hist = nullptr;
+    rq.hist_cap = 0;
+    rq.acc = &fa;
+    s = cocg_core(ctx, rq, nullptr, &it2, nullptr);
+    if (s != FTK_OK) return s;
+    if (it2 != it1) return fail(ctx, FTK_ECUDA, "ftk_filter_shells: the second pass did not replay the first");
+    // norms <phi^m|phi^m>, shell metadata (scale 1, origin E_m)
+    std::vector<double> one(L, 1.0);
+    CK(cudaMemcpyAsync(ctx->shell_scale + first_shell, one.data(), sizeof(double) * L, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    if ((int)ctx->shell_step.size() < first_shell + L) {
+        ctx->shell_step.resize(first_shell + L, -1);
+        ctx->shell_origin.resize(first_shell + L, NAN);
+    }
+    for (int m = 0; m < L; ++m) {
+        InitArgs ia{};
+        ia.dim = ctx->dim;
+        ia.partials = (double *)wsp(ctx, ctx->L.partials);
+        ia.counter = &ctx->dsmall->counters[0];
+        ia.result = ctx->dsmall->op_dots + 2;
+        LAUNCH(launch_norm(FTK_FP64, phi + size_t(m) * ctx->dim, ia, vec_grid(ctx, ctx->dim), ctx->stream));
+        double n2 = 0;
+        CK(cudaMemcpyAsync(&n2, ctx->dsmall->op_dots + 2, sizeof n2, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (norm2_out) norm2_out[m] = n2;
+        ctx->shell_step[first_shell + m] = -1;
+        ctx->shell_origin[first_shell + m] = e_b + (2 * m + 1) * eps;
+    }
+    ctx->n_saved = std::max(ctx->n_saved, first_shell + L);
+    if (iters_out) *iters_out = it1;
+    return FTK_OK;
+}
+
+ftk_status ftk_filter_spectrum(ftk_ctx *ctx, const double *Gh, int32_t n_shell, int32_t n_omega, const double *energy,
+                               const double *norm2, double beta, double eps, const double *T, int32_t n_T,
+                               double *S_out, double *P_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (!Gh || !energy || !norm2 || !T || !S_out || n_shell < 1 || n_shell > 1024 || n_omega < 1 ||
+        n_omega > FTK_MAX_OMEGA || n_T < 1 || n_T > 1024 || !std::isfinite(beta) || !(eps > 0))
+        return fail(ctx, FTK_EINVAL, "bad filter spectrum arguments");
+    for (int t = 0; t < n_T; ++t)
+        if (!(T[t] > 0)) return fail(ctx, FTK_EINVAL, "temperatures must be positive");
+    for (int q = 0; q < n_shell; ++q)
+        if (!std::isfinite(energy[q]) || !(norm2[q] >= 0)) return fail(ctx, FTK_EINVAL, "bad shell energy or norm");
+    double *gb = (double *)wsp(ctx, ctx->L.gbuf);
+    double *tb = (double *)wsp(ctx, ctx->L.tbuf);
+    double *eb = tb + 1024, *nb = tb + 2048;
+    const size_t s_need = size_t(n_T) * n_omega * 8 + size_t(n_T) * n_shell * 8 + 16;
+    const size_t g_used = align_up(size_t(16) * n_shell * n_omega);
+    double *sb = (double *)wsp(ctx, ctx->L.kry[0]);
+    if (ctx->L.vec_bytes * ctx->max_rhs < s_need) {
+        if (g_used + s_need > ctx->L.tbuf - ctx->L.gbuf)
+            return fail(ctx, FTK_ENOMEM, "no workspace region large enough to stage the spectrum");
+        sb = (double *)wsp(ctx, ctx->L.gbuf + g_used);
+    }
+    double *pb = sb + size_t(n_T) * n_omega;
+    CK(cudaMemcpyAsync(gb, Gh, size_t(16) * n_shell * n_omega, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(tb, T, sizeof(double) * n_T, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(eb, energy, sizeof(double) * n_shell, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(nb, norm2, sizeof(double) * n_shell, cudaMemcpyHostToDevice, ctx->stream));
+    FrwArgs fa{};
+    fa.n_shell = n_shell;
+    fa.n_omega = n_omega;
+    fa.beta = beta;
+    fa.eps = eps;
+    fa.E = eb;
+    fa.norm2 = nb;
+    fa.G = gb;
+    fa.T = tb;
+    fa.S = sb;
+    fa.P = pb;
+    LAUNCH(launch_frw_spectrum(fa, n_T, ctx->stream));
+    CK(cudaMemcpyAsync(S_out, sb, sizeof(double) * n_T * n_omega, cudaMemcpyDeviceToHost, ctx->stream));
+    if (P_out) CK(cudaMemcpyAsync(P_out, pb, sizeof(double) * n_T * n_shell, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return FTK_OK;
+}
+
 ftk_status ftk_spectrum(ftk_ctx *ctx, const double *Gh, int32_t n_shell, int32_t n_omega, const double *T,
                         int32_t n_T, double *S_out, int32_t *trunc_out) {
     ftk_status s = check_ready(ctx);
@@ -788,6 +1264,12 @@ ftk_status ftk_spectrum(ftk_ctx *ctx, const double *Gh, int32_t n_shell, int32_t
         return fail(ctx, FTK_EINVAL, "bad spectrum arguments");
     for (int t = 0; t < n_T; ++t)
         if (!(T[t] > 0)) return fail(ctx, FTK_EINVAL, "temperatures must be positive");
+    // the reweighting reads the mTPQ statistics of every step k < ctx->k: the
+    // shells must be the mTPQ shells 0 .. n_shell-1 of the current sequence
+    if (ctx->k < 1 || !ctx->stats) return fail(ctx, FTK_EBUSY, "no mTPQ statistics: run ftk_tpq_step first");
+    for (int q = 0; q < n_shell; ++q)
+        if (ctx->shell_step[q] != q * ctx->save_every)
+            return fail(ctx, FTK_EINVAL, "ftk_spectrum reweights mTPQ shells (use ftk_filter_spectrum for filtered ones)");
     double *gb = (double *)wsp(ctx, ctx->L.gbuf);
     double *tb = (double *)wsp(ctx, ctx->L.tbuf);
     // S and trunc are staged in the Krylov region or, for small clusters,
@@ -855,7 +1337,7 @@ ftk_status ftk_get_vector(ftk_ctx *ctx, int32_t which, double *host_out) {
         scale = &ctx->dsmall->tpq.scale;
     } else if (which > 0) {
         const int sh = which - 1;
-        if (sh >= ctx->n_saved) return fail(ctx, FTK_EINVAL, "no such shell");
+        if (!shell_written(ctx, sh)) return fail(ctx, FTK_EINVAL, "no such shell");
         src = wsp(ctx, ctx->L.shells + ctx->L.vec_bytes * sh);
         scale = ctx->shell_scale + sh;
     } else {
@@ -983,6 +1465,7 @@ void ftk_destroy(ftk_ctx *ctx) {
     if (ctx->shell_scale) cudaFree(ctx->shell_scale);
     if (ctx->slot_energy) cudaFree(ctx->slot_energy);
     if (ctx->slot_norm2) cudaFree(ctx->slot_norm2);
+    if (ctx->cocg_exec) cudaGraphExecDestroy(ctx->cocg_exec);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

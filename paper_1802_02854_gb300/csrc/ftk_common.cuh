@@ -96,7 +96,14 @@ struct CocgSeed {
     int32_t done;               // 1 converged, 2 r^T r vanished, 3 alpha denominator
                                 // vanished, 4 max_iter, 5 non-finite residual
     int32_t iters;              // iterations accumulated into G
-    int32_t pad;
+    int32_t seed_idx;           // shift that is the seed system (moves when the seed switches)
+    // Seed switching (the seed converged, shifts remain): this iteration the
+    // slowest shift s* became the seed; r_k and w_k are scaled by s1 = 1/pi*_k,
+    // r_{k-1} by s0 = 1/pi*_{k-1} (the switch kernel does it), the pi of every
+    // shift likewise
+    int32_t sw;                 // 1: switched in this iteration
+    int32_t switches;           // number of switches so far
+    double s1_re, s1_im, s0_re, s0_im;
 };
 
 // Dots produced by the vector kernels for each RHS (reduced, double).

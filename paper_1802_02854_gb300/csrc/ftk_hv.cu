@@ -157,7 +157,8 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
     // exact FMA two-products and two-sums (double-float, ~48 bits) on the
     // FP32 pipe
     constexpr bool MIX = EPI == EPI_COCG_MIXED;
-    constexpr int ND = (EPI == EPI_TPQ) ? 2 : ((EPI == EPI_COCG || MIX) ? 2 * B : 1);
+    constexpr int ND = (EPI == EPI_TPQ || EPI == EPI_TAYLOR) ? 2 : ((EPI == EPI_COCG || MIX) ? 2 * B : 1);
+    const R tcoef = (EPI == EPI_TAYLOR) ? (R)ea.tcoef : (R)0;
     Acc<R> dot[ND];
     const bool first = pd.first != 0;
 
@@ -274,6 +275,21 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                     dot[0].fma2(pim[k][0], ai[k][0]);
                     dot[1].fma2(yr, yr);
                     dot[1].fma2(yi, yi);
+                } else if constexpr (EPI == EPI_TAYLOR) {
+                    // cTPQ Taylor term: t' = c (l v - H v / N), acc += t';
+                    // <v|Hv> (the energy of v), |acc|^2
+                    const R yr = tcoef * (ell * pr[k][0] - inv_n * ar[k][0]);
+                    const R yi = tcoef * (ell * pim[k][0] - inv_n * ai[k][0]);
+                    ok[0] = mk<R>(yr, yi);
+                    cx *ap = reinterpret_cast<cx *>(ea.taylor_acc) + tofs + eofs(k);
+                    cx a = *ap;
+                    a.x += yr;
+                    a.y += yi;
+                    *ap = a;
+                    dot[0].fma2(pr[k][0], ar[k][0]);
+                    dot[0].fma2(pim[k][0], ai[k][0]);
+                    dot[1].fma2(a.x, a.x);
+                    dot[1].fma2(a.y, a.y);
                 } else if constexpr (EPI == EPI_COCG) {
                     // W = H R;  mu_j = R_j^T W_j (bilinear)
 #pragma unroll
@@ -796,6 +812,8 @@ static cudaError_t attrs_le() {
         if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, B, LE, EPI_COCG_MIXED>);
     if constexpr (B == 1)
         if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, 1, LE, EPI_TPQ>);
+    if constexpr (B == 1 && sizeof(R) == 8)
+        if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, 1, LE, EPI_TAYLOR>);
     return e;
 }
 
@@ -853,6 +871,8 @@ static cudaError_t launch_le(int epi, const void *in, void *out, long long ld, c
     }
     else if constexpr (B == 1) {
         if (epi == EPI_TPQ) k = hv_pass_kernel<R, 1, LE, EPI_TPQ>;
+        if constexpr (sizeof(R) == 8)
+            if (epi == EPI_TAYLOR) k = hv_pass_kernel<R, 1, LE, EPI_TAYLOR>;
     }
     if (!k) return cudaErrorInvalidValue;
     const int threads = hv_threads(pd);
@@ -960,7 +980,8 @@ cudaError_t launch_hv_pass(int prec, int B, int epi, const void *in, void *out, 
     const int bc = pd.cols;
     if (B < 1 || (B & (B - 1)) || B > FTK_MAX_RHS || bc < 1 || bc > hv_max_b(prec) || (B % bc) ||
         pd.le != hv_le(prec, bc, pd.tile_bits, pd.chunk_bits) || hv_threads(pd) > 512 ||
-        (epi == EPI_TPQ && B != 1) || (ea.lo && prec != 1) || (prec == 2 && ea.df_lo <= 0))
+        ((epi == EPI_TPQ || epi == EPI_TAYLOR) && B != 1) || (epi == EPI_TAYLOR && (prec != 0 || !ea.taylor_acc)) ||
+        (ea.lo && prec != 1) || (prec == 2 && ea.df_lo <= 0))
         return cudaErrorInvalidConfiguration;
     if (prec == 2) return launch_hv_pass_df(B, epi, in, out, pd, ea, grid_cap, st);
     const size_t es = prec == 0 ? 16 : 8;

@@ -70,16 +70,18 @@ __global__ void __launch_bounds__(256) cocg_update_kernel(V vec, UpdArgs ua) {
         c_re = (R)s.c_re; c_im = (R)s.c_im;
     }
     const cx *lam = reinterpret_cast<const cx *>(ua.lambda[j]);
+    // g = proj^dag r: the projection vector (A of <A|(z - H)^-1|B>), lambda by default
+    const cx *prj = ua.proj[j] ? reinterpret_cast<const cx *>(ua.proj[j]) : lam;
     // range guard of the seed kernel: r_{k+1} and r_k (the next r_{k-1}) scaled by f
     const R f = ua.mode == 1 ? (R)ua.seed[j].rescale : (R)1;
     Acc<R> d_rr, d_ri, d_gr, d_gi, d_n;
     if (!skip) {
         for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
              x += (uint64_t)gridDim.x * blockDim.x) {
-            const cx l = lam[x];
+            const cx l = prj[x];
             cx r;
             if (ua.mode == 0) {
-                r = l;
+                r = lam[x];
             } else {
                 const cx rc = vec.load_r(off + x), wc = vec.load_w(off + x), rp = vec.load_rp(off + x);
                 // A r = z_s r - w (the lo terms of z_s vanish in double)
@@ -170,7 +172,10 @@ cocg_update_df_kernel(float2 *rcur, const float2 *__restrict__ w, float2 *rnew, 
             if (ua.mode == 0) {
                 const double2 ld = lam[x];
                 r = {dfl_from(ld.x), dfl_from(ld.y)};
-                l4 = make_float4(r.re.hi, r.im.hi, r.re.lo, r.im.lo);
+                // the projection vector's split (lambda's unless another is given)
+                const double2 pv = ua.proj[j] ? reinterpret_cast<const double2 *>(ua.proj[j])[x] : ld;
+                const dfl pr = dfl_from(pv.x), pim = dfl_from(pv.y);
+                l4 = make_float4(pr.hi, pim.hi, pr.lo, pim.lo);
                 lsp[x] = l4;
             } else {
                 l4 = lsp[x];
@@ -238,6 +243,7 @@ __global__ void cocg_seed_kernel(SeedArgs sa) {
     const int j = threadIdx.x;
     if (j < sa.n_rhs) {
         CocgSeed &s = sa.seed[j];
+        s.sw = 0;
         if (!s.done) seed_one(sa, s, j);
     }
     __syncthreads();
@@ -259,7 +265,7 @@ __device__ void seed_one(const SeedArgs &sa, CocgSeed &s, int j) {
     const double *ud = sa.upd + j * FTK_UPD_DOTS;
     const double *hd = sa.hv + j * FTK_HV_DOTS;
     dcx rho = {ud[0], ud[1]}, g = {ud[2], ud[3]}, mu = {hd[0], hd[1]};
-    const double nrm = sqrt(fmax(ud[4], 0.0));
+    double nrm = sqrt(fmax(ud[4], 0.0));
     const int k = s.k;
     if (k == 0) s.lnorm = nrm;
     // the shift kernel of iteration k-1 wrote max 1/|pi_k| into parity k;
@@ -277,6 +283,48 @@ __device__ void seed_one(const SeedArgs &sa, CocgSeed &s, int j) {
         return;
     }
     if (nrm == 0.0 || s.lnorm == 0.0) { s.done = 1; return; }     // exact solution
+    if (sa.seed_switch && k >= 1 && nrm <= sa.tol * s.lnorm) {
+        // Seed switching: the seed system has converged while other shifts
+        // have not (else the test above would have stopped the solve). The
+        // unconverged shift with the largest residual ||r_k|| / |pi^s_k|, i.e.
+        // the smallest |pi^s_k|, becomes the seed. Only residuals enter the
+        // recurrences, so with s1 = 1/pi*_k and s0 = 1/pi*_{k-1} the switch is
+        // exact: r_k, w_k, g_k scale by s1, r_{k-1} by s0, rho_k and mu_k by
+        // s1^2, rho_{k-1} by s0^2, alpha_{k-1} becomes the shift's
+        // alpha*_{k-1} = alpha_{k-1} s1 / s0, and every pi^s_k, pi^s_{k-1} is
+        // divided by pi*_k, pi*_{k-1} (the switch kernel scales the vectors
+        // and the pi arrays); G, p~ and every shifted residual are unchanged.
+        const dcx *pc = sa.pi_cur + (size_t)j * sa.n_omega;
+        const dcx *pp = sa.pi_prev + (size_t)j * sa.n_omega;
+        const int *fz = sa.frozen + (size_t)j * sa.n_omega;
+        const double lim = nrm / (sa.tol * s.lnorm);   // unconverged: |pi| < lim
+        int best = -1;
+        double bmin = lim;
+        for (int q = 0; q < sa.n_omega; ++q) {
+            if (fz[q]) continue;
+            const double a = cabs_(pc[q]);
+            if (a < bmin) { bmin = a; best = q; }
+        }
+        if (best >= 0 && best != s.seed_idx) {
+            const dcx one = {1.0, 0.0};
+            const dcx s1 = cdiv(one, pc[best]), s0 = cdiv(one, pp[best]);
+            const dcx s1s = cmul(s1, s1), s0s = cmul(s0, s0);
+            rho = cmul(rho, s1s);
+            mu = cmul(mu, s1s);
+            g = cmul(g, s1);
+            nrm *= cabs_(s1);
+            const dcx rp = cmul({s.rho_re, s.rho_im}, s0s);
+            s.rho_re = rp.re; s.rho_im = rp.im;
+            const dcx ap = cmul({s.alpha_re, s.alpha_im}, cdiv(s1, s0));
+            s.alpha_re = ap.re; s.alpha_im = ap.im;
+            s.zs_re = s.e0 + sa.shift[best].re;
+            s.zs_im = sa.shift[best].im;
+            s.seed_idx = best;
+            s.sw = 1;
+            s.s1_re = s1.re; s.s1_im = s1.im; s.s0_re = s0.re; s.s0_im = s0.im;
+            s.switches += 1;
+        }
+    }
     // r^T r vanished: at a residual 1e-12 below ||lambda|| this is the
     // underflow of FP32 vectors (the seed system is solved far beyond any
     // shifted one can still gain): stop as converged; otherwise a breakdown
@@ -338,12 +386,18 @@ __global__ void cocg_shift_kernel(ShiftArgs sh) {
         const dcx pc0 = sh.pi_cur[o];
         if (s.nrm <= sh.tol * s.lnorm * cabs_(pc0)) { sh.frozen[o] = 1; active = false; }
     }
+    // history (right-hand side 0): iteration k = s.k - 1 of a running solve
+    const int kh = s.k - 1;
+    dcx* hrec = (sh.hist && j == 0 && !s.done && si < sh.n_omega && kh >= 0 && kh < sh.hist_cap)
+                    ? sh.hist + ((size_t)kh * sh.n_omega + si) * 3 : nullptr;
+    if (hrec) { hrec[0] = {0.0, 0.0}; hrec[1] = {0.0, 0.0}; hrec[2] = {0.0, 0.0}; }
     if (active) {
         const int k = s.k - 1;   // iteration just computed by the seed kernel
         dcx pc = sh.pi_cur[o], pp = sh.pi_prev[o], pt = sh.ptil[o], G = sh.G[o];
         const dcx alpha = {s.alpha_re, s.alpha_im}, c = {s.c_re, s.c_im};
         const dcx beta = {s.beta_prev_re, s.beta_prev_im}, g = {s.g_re, s.g_im};
-        const dcx D = {sh.omega[si] - sh.omega[sh.seed_idx], 0.0};
+        const dcx zs = sh.shift[s.seed_idx], zo = sh.shift[si];
+        const dcx D = {zo.re - zs.re, zo.im - zs.im};
         dcx bs = {0, 0};
         if (k >= 1) { dcx r = cdiv(pp, pc); bs = cmul(cmul(r, r), beta); }
         dcx gp = cdiv(g, pc), bp = cmul(bs, pt);
@@ -355,6 +409,7 @@ __global__ void cocg_shift_kernel(ShiftArgs sh) {
         dcx as = cdiv(cmul(alpha, pc), pn);
         dcx ag = cmul(as, pt);
         G.re += ag.re; G.im += ag.im;
+        if (hrec) { hrec[0] = as; hrec[1] = bs; hrec[2] = cdiv({1.0, 0.0}, pc); }
         const double f = s.rescale;   // range guard of the seed kernel (1 or a power of two)
         pc.re *= f; pc.im *= f; pn.re *= f; pn.im *= f;
         sh.pi_prev[o] = pc; sh.pi_cur[o] = pn; sh.ptil[o] = pt; sh.G[o] = G;
@@ -370,6 +425,116 @@ __global__ void cocg_shift_kernel(ShiftArgs sh) {
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
         atomicMax(reinterpret_cast<unsigned long long *>(sh.inv_pi_max + ((s.k & 1) * FTK_MAX_RHS) + j),
                   (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// ------------------------------------------------------------ seed switch
+// Applies the scalings of a seed switch decided by the seed kernel (see
+// seed_one): r_k and w_k times s1, r_{k-1} times s0, and pi^s_k, pi^s_{k-1}
+// of every shift of that right-hand side likewise. A right-hand side without
+// a switch in this iteration returns at once (the usual case).
+__device__ __forceinline__ dcl dcl_of(double re, double im) { return {dfl_from(re), dfl_from(im)}; }
+__global__ void __launch_bounds__(256) cocg_switch_kernel(SwitchArgs sw) {
+    if (*sw.all_done) return;
+    const int j = blockIdx.y;
+    const CocgSeed &s = sw.seed[j];
+    if (!s.sw) return;
+    const dcx s1 = {s.s1_re, s.s1_im}, s0 = {s.s0_re, s.s0_im};
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint64_t q = t0; q < (uint64_t)sw.n_omega; q += stride) {
+        const size_t o = (size_t)j * sw.n_omega + q;
+        sw.pi_cur[o] = cmul(sw.pi_cur[o], s1);
+        sw.pi_prev[o] = cmul(sw.pi_prev[o], s0);
+    }
+    const size_t off = (size_t)j * sw.dim;
+    if (sw.kind == 0) {
+        double2 *rc = reinterpret_cast<double2 *>(sw.rcur) + off, *rp = reinterpret_cast<double2 *>(sw.rprev) + off;
+        double2 *w = reinterpret_cast<double2 *>(sw.w) + off;
+        for (uint64_t x = t0; x < sw.dim; x += stride) {
+            const dcx a = cmul({rc[x].x, rc[x].y}, s1), b = cmul({rp[x].x, rp[x].y}, s0), c = cmul({w[x].x, w[x].y}, s1);
+            rc[x] = make_double2(a.re, a.im); rp[x] = make_double2(b.re, b.im); w[x] = make_double2(c.re, c.im);
+        }
+    } else if (sw.kind == 1) {
+        float2 *rc = reinterpret_cast<float2 *>(sw.rcur) + off, *rp = reinterpret_cast<float2 *>(sw.rprev) + off;
+        float2 *w = reinterpret_cast<float2 *>(sw.w) + off;
+        for (uint64_t x = t0; x < sw.dim; x += stride) {
+            const dcx a = cmul({rc[x].x, rc[x].y}, s1), b = cmul({rp[x].x, rp[x].y}, s0), c = cmul({w[x].x, w[x].y}, s1);
+            rc[x] = make_float2((float)a.re, (float)a.im); rp[x] = make_float2((float)b.re, (float)b.im);
+            w[x] = make_float2((float)c.re, (float)c.im);
+        }
+    } else {
+        // float hi + lo pairs: products in double-float arithmetic
+        const long long lo = sw.lo_stride;
+        float2 *rc = reinterpret_cast<float2 *>(sw.rcur) + off, *rp = reinterpret_cast<float2 *>(sw.rprev) + off;
+        float2 *w = reinterpret_cast<float2 *>(sw.w) + off;
+        const dcl f1 = dcl_of(s1.re, s1.im), f0 = dcl_of(s0.re, s0.im);
+        for (uint64_t x = t0; x < sw.dim; x += stride) {
+            const dcl a = dcl_mul({{rc[x].x, rc[x + lo].x}, {rc[x].y, rc[x + lo].y}}, f1);
+            const dcl b = dcl_mul({{rp[x].x, rp[x + lo].x}, {rp[x].y, rp[x + lo].y}}, f0);
+            rc[x] = make_float2(a.re.hi, a.im.hi); rc[x + lo] = make_float2(a.re.lo, a.im.lo);
+            rp[x] = make_float2(b.re.hi, b.im.hi); rp[x + lo] = make_float2(b.re.lo, b.im.lo);
+            if (sw.w_lo) {
+                const dcl c = dcl_mul({{w[x].x, w[x + sw.w_lo].x}, {w[x].y, w[x + sw.w_lo].y}}, f1);
+                w[x] = make_float2(c.re.hi, c.im.hi); w[x + sw.w_lo] = make_float2(c.re.lo, c.im.lo);
+            } else {
+                const dcx c = cmul({w[x].x, w[x].y}, s1);
+                w[x] = make_float2((float)c.re, (float)c.im);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ contour filter
+// Second pass of the filter solve: phi_m += C[k][m] r_k for every centre m
+// (FP64 vectors; k = iteration just computed, skipped once the solve is done).
+__global__ void __launch_bounds__(256) filter_acc_kernel(FilterAccArgs fa) {
+    const CocgSeed &s = *fa.seed;
+    if (s.done) return;
+    const int k = s.k - 1;
+    if (k < 0 || k >= fa.n_coef) return;
+    const dcx *c = fa.coef + (size_t)k * fa.L;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < fa.dim;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const double2 r = fa.r[x];
+        for (int m = 0; m < fa.L; ++m) {
+            const dcx cm = c[m];
+            double2 *p = fa.phi + (size_t)m * fa.dim + x;
+            double2 v = *p;
+            v.x = fma(cm.re, r.x, fma(-cm.im, r.y, v.x));
+            v.y = fma(cm.re, r.y, fma(cm.im, r.x, v.y));
+            *p = v;
+        }
+    }
+}
+
+// Filter coefficients: one CTA (one warp) per centre m, lane j < M the shift
+// s = m M + j. Backward over the recorded iterations,
+//   T^s_k = alpha^s_k + b^s_{k+1} T^s_{k+1}   (b^s_l = beta^s_{l-1}),
+// so that x^s = sum_k (T^s_k / pi^s_k) r_k, and C[k][m] = sum_j w_j T^s_k / pi^s_k
+// (warp sum in a fixed order).
+__global__ void __launch_bounds__(32) filter_coef_kernel(FilterCoefArgs fc) {
+    const int m = blockIdx.x, j = threadIdx.x;
+    const bool on = j < fc.M;
+    const size_t ns = (size_t)fc.L * fc.M;
+    const size_t sidx = (size_t)m * fc.M + (on ? j : 0);
+    const dcx wj = on ? fc.w[j] : dcx{0.0, 0.0};
+    dcx T = {0.0, 0.0};
+    for (int k = fc.n_iter - 1; k >= 0; --k) {
+        dcx v = {0.0, 0.0};
+        if (on) {
+            const dcx *h = fc.hist + ((size_t)k * ns + sidx) * 3;
+            const dcx bnext = (k + 1 < fc.n_iter) ? fc.hist[((size_t)(k + 1) * ns + sidx) * 3 + 1] : dcx{0.0, 0.0};
+            const dcx bt = cmul(bnext, T);
+            T = {h[0].re + bt.re, h[0].im + bt.im};
+            v = cmul(wj, cmul(T, h[2]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+            v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+        }
+        if (j == 0) fc.coef[(size_t)k * fc.L + m] = v;
     }
 }
 
@@ -597,7 +762,51 @@ __global__ void __launch_bounds__(256) spectrum_kernel(SpecArgs sp) {
     }
 }
 
+// ------------------------------------------------- filter-shell reweighting
+__global__ void __launch_bounds__(256) frw_spectrum_kernel(FrwArgs fa) {
+    __shared__ double red[(256 / 32) * 1];
+    const int t = blockIdx.x;
+    const double db = fa.beta - 1.0 / fa.T[t];
+    double m = -INFINITY;
+    for (int q = threadIdx.x; q < fa.n_shell; q += blockDim.x)
+        if (fa.norm2[q] > 0.0) m = fmax(m, db * fa.E[q] + log(fa.norm2[q]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[w]);
+        double z = 0.0;   // fixed-order sum
+        for (int q = 0; q < fa.n_shell; ++q)
+            if (fa.norm2[q] > 0.0) z += exp(db * fa.E[q] + log(fa.norm2[q]) - mm);
+        red[0] = mm;
+        red[1] = z;
+    }
+    __syncthreads();
+    const double mx = red[0], z = red[1];
+    if (fa.P)
+        for (int q = threadIdx.x; q < fa.n_shell; q += blockDim.x)
+            fa.P[(size_t)t * fa.n_shell + q] =
+                fa.norm2[q] > 0.0 ? exp(db * fa.E[q] + log(fa.norm2[q]) - mx) / (2.0 * fa.eps * z) : 0.0;
+    for (int w = threadIdx.x; w < fa.n_omega; w += blockDim.x) {
+        double acc = 0.0;
+        // e^{db E_q} G_q = e^{db E_q + log n_q - mx} (G_q / n_q) e^{mx}: no
+        // overflow for shells of tiny weight (G_q scales with n_q)
+        for (int q = 0; q < fa.n_shell; ++q)
+            if (fa.norm2[q] > 0.0)
+                acc += exp(db * fa.E[q] + log(fa.norm2[q]) - mx) *
+                       (-fa.G[2 * ((size_t)q * fa.n_omega + w) + 1] / M_PI / fa.norm2[q]);
+        fa.S[(size_t)t * fa.n_omega + w] = acc / z;
+    }
+}
+
 // ================================================================ launchers
+cudaError_t launch_frw_spectrum(const FrwArgs &fa, int n_T, cudaStream_t st) {
+    frw_spectrum_kernel<<<n_T, 256, 0, st>>>(fa);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cocg_update(int kind, int B, void *rcur, const void *w, void *rprev_new,
                                const UpdArgs &ua, int grid, cudaStream_t st) {
     if (B < 1 || B > FTK_MAX_RHS) return cudaErrorInvalidValue;
@@ -625,6 +834,22 @@ cudaError_t launch_cocg_seed(const SeedArgs &sa, cudaStream_t st) {
 cudaError_t launch_cocg_shift(const ShiftArgs &sh, int n_rhs, cudaStream_t st) {
     dim3 grid((sh.n_omega + 255) / 256, n_rhs);
     cocg_shift_kernel<<<grid, 256, 0, st>>>(sh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cocg_switch(const SwitchArgs &sw, int B, int grid, cudaStream_t st) {
+    cocg_switch_kernel<<<dim3(grid, B), 256, 0, st>>>(sw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_acc(const FilterAccArgs &fa, int grid, cudaStream_t st) {
+    filter_acc_kernel<<<grid, 256, 0, st>>>(fa);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_coef(const FilterCoefArgs &fc, cudaStream_t st) {
+    if (fc.M < 1 || fc.M > 32 || fc.L < 1) return cudaErrorInvalidValue;
+    filter_coef_kernel<<<fc.L, 32, 0, st>>>(fc);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,7 @@
 
 namespace ftk {
 
-enum { EPI_PLAIN = 0, EPI_TPQ = 1, EPI_COCG = 2, EPI_COCG_MIXED = 3 };
+enum { EPI_PLAIN = 0, EPI_TPQ = 1, EPI_COCG = 2, EPI_COCG_MIXED = 3, EPI_TAYLOR = 4 };
 
 struct EpiArgs {
     const double *scale;     // TPQ: device s_k
@@ -16,6 +16,10 @@ struct EpiArgs {
     double *stat_u, *stat_logq, *stat_h2;   // TPQ statistics arrays [k]
     const int *all_done;     // COCG: skip when every RHS finished (or NULL)
     const void *lo;          // COCG, mixed mode: float2 low parts of the input (mu from hi + lo)
+    // Taylor term of the cTPQ series (Appendix A, FP64, one vector):
+    // out = tcoef (l v - H v / N), taylor_acc += out; dots <v|H v>, |acc|^2
+    double2 *taylor_acc;
+    double tcoef;
     long long df_lo;         // double-float mode: float2 offset of the lo arrays of in and out
     // Double-float mode, first pass of H r_{k+1}: the COCG residual update
     // fused in (fu_seed != NULL). Per launch (one column): the pass's input
@@ -39,6 +43,10 @@ struct UpdArgs {
     int mode;                // 0: r = lambda, 1: 3-term update
     uint64_t dim;
     const void *lambda[FTK_MAX_RHS];
+    // projection vector of g = proj^dag r (the A of <A|(z - H)^-1|B>, Sec. II.B);
+    // NULL: the right-hand side itself. Mixed / double-float modes: mode 0
+    // writes the split of proj (not of lambda) to lam_split.
+    const void *proj[FTK_MAX_RHS];
     const CocgSeed *seed;
     double *partials;
     unsigned int *counter;
@@ -63,17 +71,86 @@ struct SeedArgs {
     int *all_done;
     double relax;            // relaxed solve: theta (0: off)
     int *lowp;               // set (sticky) once every running RHS has resid < theta
+    // seed switching (seed_switch = 1): the shift offsets and the shift state
+    // of the block, read when the seed has converged before the other shifts
+    int seed_switch;
+    int n_omega;
+    const struct dcx *shift;            // [n_omega] z_s - E_j (complex offsets)
+    const struct dcx *pi_prev, *pi_cur; // [B][n_omega]
+    const int *frozen;                  // [B][n_omega]
 };
 
+// Shift s of right-hand side j is z_js = E_j + shift[s] (complex; the
+// spectrum solves use shift[s] = omega_s + i eta, the contour filter
+// E_m + eps e^{i theta} - E_j).
 struct ShiftArgs {
     int n_omega;
-    int seed_idx;
-    const double *omega;     // [n_omega]
+    const struct dcx *shift; // [n_omega]
     const CocgSeed *seed;
     struct dcx *pi_prev, *pi_cur, *ptil, *G;   // [B][n_omega]
     double *inv_pi_max;      // [2][FTK_MAX_RHS]
     int *frozen;             // [B][n_omega] converged shifts
     double tol;
+    // history of the shift recurrences (right-hand side 0 only; NULL: off):
+    // per iteration k and shift s, (alpha^s_k, beta^s_{k-1}, 1/pi^s_k) with
+    // alpha^s_k = 0 when the shift no longer contributes; hist_cap iterations
+    struct dcx *hist;
+    int hist_cap;
+};
+
+// Seed switch: scale r_k, w_k by s1 and r_{k-1} by s0 for every right-hand
+// side whose seed switched in this iteration (CocgSeed::sw), and pi_k,
+// pi_{k-1} of all its shifts likewise. kind as launch_cocg_update.
+struct SwitchArgs {
+    int kind;
+    uint64_t dim;
+    void *rcur, *rprev, *w;
+    long long lo_stride;     // mixed / double-float: float2 offset of the lo parts
+    long long w_lo;          // double-float: lo part of w (0: w is float)
+    CocgSeed *seed;
+    struct dcx *pi_prev, *pi_cur;
+    int n_omega;
+    const int *all_done;
+};
+
+// Contour filter, second pass: phi_m += C[k][m] r_k for every shell centre
+// m < L (one right-hand side, FP64 vectors), k = the current iteration.
+struct FilterAccArgs {
+    uint64_t dim;
+    int L;
+    int n_coef;              // iterations in coef (a later iteration adds nothing)
+    const double2 *r;        // r_k
+    double2 *phi;            // [L][dim]
+    const struct dcx *coef;  // [iterations][L]
+    const CocgSeed *seed;    // iteration index and status of the solve
+};
+
+// Contour filter, coefficients: from the recorded history, per shift s the
+// backward sum T^s_k = alpha^s_k + beta^s_k T^s_{k+1} (beta^s_k = the
+// beta^s of iteration k + 1), C^s_k = T^s_k / pi^s_k, and per centre m
+// C[k][m] = sum_{j < M} w_j C^{(m, j)}_k with shift index s = m M + j.
+// Reweighting of filter shells (Eqs. FRW1, FRW2), one CTA per temperature:
+//   S(omega, T) = sum_m e^{(b - b')E_m} (-Im G_m(omega) / pi) / sum_l e^{(b - b')E_l} n_l
+//   P_b'(E_m)   = e^{(b - b')E_m} n_m / (2 eps sum_l e^{(b - b')E_l} n_l)
+// with b' = 1/T, n_m = <phi^m|phi^m>, log-sum-exp in double.
+struct FrwArgs {
+    int n_shell, n_omega;
+    double beta, eps;
+    const double *E, *norm2;   // [n_shell]
+    const double *G;           // [n_shell][n_omega][2]
+    const double *T;           // [n_T]
+    double *S;                 // [n_T][n_omega]
+    double *P;                 // [n_T][n_shell]
+};
+cudaError_t launch_frw_spectrum(const FrwArgs &fa, int n_T, cudaStream_t st);
+
+struct FilterCoefArgs {
+    int n_iter;              // iterations recorded
+    int L, M;
+    const struct dcx *hist;  // [n_iter][L M][3]
+    const struct dcx *w;     // [M] quadrature weights rho e^{i theta_j} / M
+    struct dcx *tsum;        // [L M] scratch: T^s of the running iteration
+    struct dcx *coef;        // [n_iter][L]
 };
 
 struct OpArgs {
@@ -137,6 +214,9 @@ cudaError_t launch_cocg_update(int kind, int B, void *rcur, const void *w, void 
                                const UpdArgs &ua, int grid, cudaStream_t st);
 cudaError_t launch_cocg_seed(const SeedArgs &sa, cudaStream_t st);
 cudaError_t launch_cocg_shift(const ShiftArgs &sh, int n_rhs, cudaStream_t st);
+cudaError_t launch_cocg_switch(const SwitchArgs &sw, int B, int grid, cudaStream_t st);
+cudaError_t launch_filter_acc(const FilterAccArgs &fa, int grid, cudaStream_t st);
+cudaError_t launch_filter_coef(const FilterCoefArgs &fc, cudaStream_t st);
 cudaError_t launch_apply_op(int prec, const void *psi, void *lam, const OpArgs &oa, int grid,
                             cudaStream_t st);
 cudaError_t launch_init_state(int prec, void *v, const InitArgs &ia, int grid, cudaStream_t st);

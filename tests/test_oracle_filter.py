@@ -88,3 +88,37 @@ def test_green_function_closed_form():
             ref[i] += np.sum(np.abs(a) ** 2 / (zeta + e - dg.E))
     ref /= np.vdot(phi, phi).real
     assert np.max(np.abs(got - ref)) <= 1e-9 * np.abs(ref).max()
+
+
+def test_reweighting_recovers_the_canonical_energy():
+    """Eqs. FRW1/FRW2 on a noise-free state: phi_beta = sum_n e^{-beta E_n / 2}|n>
+    (every |c_n| = 1), shells of width 2 eps = 0.02 covering the spectrum,
+    filter in closed form (M = 32). The discrete filters do not sum to one:
+    g(E) = sum_m f_m(E)^2 dips to 1/2 between centres. Reweighted to beta',
+    the energy <H> must equal the canonical average with that coverage,
+    sum_n g(E_n) e^{-beta' E_n} E_n / sum_n g(E_n) e^{-beta' E_n}, exactly at
+    beta' = beta and up to the shell-centre approximation of e^{(beta - beta') E}
+    inside a shell otherwise (|beta - beta'| eps ~ 1e-2 relative at most);
+    a wrong sign of the exponent misses by far more. FRW2 sums to one."""
+    cl = named(8)
+    dg = dense.Diag(cl, -1.0, 0.1)
+    E = dg.E
+    beta, eps, M = 1.0, 0.01, 32
+    e_b = E.min() - 10 * eps
+    L = int(np.ceil((E.max() - e_b) / (2 * eps))) + 10
+    grid = flt.energy_grid(e_b, eps, L)
+    c2 = np.exp(-beta * (E - E.min()))                   # |c_n|^2 of phi_beta (rescaled)
+    f2 = np.array([closed_form(E, g, eps, M) ** 2 for g in grid])   # [L, n]
+    g = f2.sum(axis=0)
+    norm2 = f2 @ c2
+    h_m = f2 @ (c2 * E)                                  # <phi^m|H|phi^m>
+    for beta_p in (0.5, 1.0, 2.0):
+        got, P = flt.reweight(h_m, norm2, grid, beta, beta_p, eps)
+        w = g * np.exp(-beta_p * (E - E.min()))
+        want = np.sum(w * E) / np.sum(w)
+        tol = 1e-13 if beta_p == beta else 2 * abs(beta - beta_p) * eps * np.abs(E).max()
+        assert abs(got - want) <= tol
+        assert abs(np.sum(P) * 2 * eps - 1.0) <= 1e-12
+        if beta_p != beta:
+            bad, _ = flt.reweight(h_m, norm2, grid, beta, 2 * beta - beta_p, eps)
+            assert abs(bad - want) > 10 * tol
