@@ -59,12 +59,24 @@ struct KMask {
     static constexpr int m = (KA >= 0 ? (1 << KA) : 0) | (KB >= 0 ? (1 << KB) : 0);
 };
 
+// acc += c p for a complex amplitude and a real coefficient: on sm_100 and
+// later, float pairs take one packed FMA (fma.rn.f32x2) for both components
+__device__ __forceinline__ void cfma(double c, const double2 &p, double2 &acc) {
+    acc.x = fma(c, p.x, acc.x);
+    acc.y = fma(c, p.y, acc.y);
+}
+__device__ __forceinline__ void cfma(float c, const float2 &p, float2 &acc) {
+    acc = __ffma2_rn(make_float2(c, c), p, acc);
+}
+__device__ __forceinline__ void cadd(const double2 &p, double2 &acc) { acc.x += p.x; acc.y += p.y; }
+__device__ __forceinline__ void cadd(const float2 &p, float2 &acc) { acc = __fadd2_rn(acc, p); }
+
 // acc[k] += c(k) P[k ^ km]: c = cs where the register bits of the bond are
 // parallel (k-parity 0), cf otherwise; k, k ^ km and the choice are
 // compile-time after unrolling.
 template <typename R, int B, int LE, int KA, int KB>
-__device__ __forceinline__ void bond_apply(R (&ar)[1 << LE][B], R (&ai)[1 << LE][B], const R (&pr)[1 << LE][B],
-                                           const R (&pi)[1 << LE][B], R cs, R cf) {
+__device__ __forceinline__ void bond_apply(typename C2<R>::t (&acc)[1 << LE][B], const typename C2<R>::t (&pv)[1 << LE][B],
+                                           R cs, R cf) {
     constexpr int E = 1 << LE;
 #pragma unroll
     for (int k = 0; k < E; ++k) {
@@ -72,16 +84,13 @@ __device__ __forceinline__ void bond_apply(R (&ar)[1 << LE][B], R (&ai)[1 << LE]
         const int kp = k ^ KMask<KA, KB>::m;
         const R c = kpar ? cf : cs;
 #pragma unroll
-        for (int j = 0; j < B; ++j) {
-            ar[k][j] = fma(c, pr[kp][j], ar[k][j]);
-            ai[k][j] = fma(c, pi[kp][j], ai[k][j]);
-        }
+        for (int j = 0; j < B; ++j) cfma(c, pv[kp][j], acc[k][j]);
     }
 }
 
-#define FTK_HV_CASE(ID, KA, KB)                                                                    \
-    case ID:                                                                                       \
-        if constexpr (KA < LE && KB < LE) bond_apply<R, B, LE, KA, KB>(ar, ai, pr, pim, cs, cf); \
+#define FTK_HV_CASE(ID, KA, KB)                                                             \
+    case ID:                                                                                \
+        if constexpr (KA < LE && KB < LE) bond_apply<R, B, LE, KA, KB>(acc, pv, cs, cf);    \
         break;
 
 template <typename R, int B, int LE, int EPI>
@@ -197,12 +206,12 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
         else { if (more) cp_async_wait<2>(); else cp_async_wait<1>(); }
         __syncthreads();
         if (act) {
-            R ar[E][B], ai[E][B];
-            R pr[E][B], pim[E][B];
+            cx acc[E][B];   // (re, im) accumulators
+            cx pv[E][B];    // partner amplitudes of the current group
 #pragma unroll
             for (int k = 0; k < E; ++k)
 #pragma unroll
-                for (int j = 0; j < B; ++j) { ar[k][j] = (R)0; ai[k][j] = (R)0; }
+                for (int j = 0; j < B; ++j) acc[k][j] = mk<R>((R)0, (R)0);
             int q = 0;
             for (int g = 0; g < pd.n_groups; ++g) {
                 const int tm = pd.grp_tmask[g];
@@ -210,11 +219,7 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
 #pragma unroll
                 for (int k = 0; k < E; ++k)
 #pragma unroll
-                    for (int j = 0; j < B; ++j) {
-                        const cx v = src[(size_t)j * tile_n + T * k];
-                        pr[k][j] = v.x;
-                        pim[k][j] = v.y;
-                    }
+                    for (int j = 0; j < B; ++j) pv[k][j] = src[(size_t)j * tile_n + T * k];
                 const int pt = __popc(t & tm) & 1;
                 for (const int end = pd.grp_end[g]; q < end; ++q) {
                     const R par = Coef<R>::par(pd, q), anti = Coef<R>::anti(pd, q);
@@ -244,20 +249,13 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
 #pragma unroll
             for (int k = 0; k < E; ++k)
 #pragma unroll
-                for (int j = 0; j < B; ++j) {
-                    ar[k][j] = fma(dg[k], pr[k][j], ar[k][j]);
-                    ai[k][j] = fma(dg[k], pim[k][j], ai[k][j]);
-                }
+                for (int j = 0; j < B; ++j) cfma(dg[k], pv[k][j], acc[k][j]);
             if (!first) {   // partial product of the earlier passes (own elements)
                 if (more) cp_async_wait<1>(); else cp_async_wait<0>();
 #pragma unroll
                 for (int k = 0; k < E; ++k)
 #pragma unroll
-                    for (int j = 0; j < B; ++j) {
-                        const cx p = pbuf[(size_t)j * tile_n + t + T * k];
-                        ar[k][j] += p.x;
-                        ai[k][j] += p.y;
-                    }
+                    for (int j = 0; j < B; ++j) cadd(pbuf[(size_t)j * tile_n + t + T * k], acc[k][j]);
             }
             cx *o = out + tofs;
 #pragma unroll
@@ -265,52 +263,52 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
                 cx *ok = o + eofs(k);
                 if (!pd.last || EPI == EPI_PLAIN) {
 #pragma unroll
-                    for (int j = 0; j < B; ++j) ok[(size_t)j * ld] = mk<R>(ar[k][j], ai[k][j]);
+                    for (int j = 0; j < B; ++j) ok[(size_t)j * ld] = acc[k][j];
                 } else if constexpr (EPI == EPI_TPQ) {
                     // psi' = s (l v - H v / N);  <v|Hv>, |psi'|^2
-                    const R yr = scale * (ell * pr[k][0] - inv_n * ar[k][0]);
-                    const R yi = scale * (ell * pim[k][0] - inv_n * ai[k][0]);
+                    const R yr = scale * (ell * pv[k][0].x - inv_n * acc[k][0].x);
+                    const R yi = scale * (ell * pv[k][0].y - inv_n * acc[k][0].y);
                     ok[0] = mk<R>(yr, yi);
-                    dot[0].fma2(pr[k][0], ar[k][0]);
-                    dot[0].fma2(pim[k][0], ai[k][0]);
+                    dot[0].fma2(pv[k][0].x, acc[k][0].x);
+                    dot[0].fma2(pv[k][0].y, acc[k][0].y);
                     dot[1].fma2(yr, yr);
                     dot[1].fma2(yi, yi);
                 } else if constexpr (EPI == EPI_TAYLOR) {
                     // cTPQ Taylor term: t' = c (l v - H v / N), acc += t';
                     // <v|Hv> (the energy of v), |acc|^2
-                    const R yr = tcoef * (ell * pr[k][0] - inv_n * ar[k][0]);
-                    const R yi = tcoef * (ell * pim[k][0] - inv_n * ai[k][0]);
+                    const R yr = tcoef * (ell * pv[k][0].x - inv_n * acc[k][0].x);
+                    const R yi = tcoef * (ell * pv[k][0].y - inv_n * acc[k][0].y);
                     ok[0] = mk<R>(yr, yi);
                     cx *ap = reinterpret_cast<cx *>(ea.taylor_acc) + tofs + eofs(k);
                     cx a = *ap;
                     a.x += yr;
                     a.y += yi;
                     *ap = a;
-                    dot[0].fma2(pr[k][0], ar[k][0]);
-                    dot[0].fma2(pim[k][0], ai[k][0]);
+                    dot[0].fma2(pv[k][0].x, acc[k][0].x);
+                    dot[0].fma2(pv[k][0].y, acc[k][0].y);
                     dot[1].fma2(a.x, a.x);
                     dot[1].fma2(a.y, a.y);
                 } else if constexpr (EPI == EPI_COCG) {
                     // W = H R;  mu_j = R_j^T W_j (bilinear)
 #pragma unroll
                     for (int j = 0; j < B; ++j) {
-                        ok[(size_t)j * ld] = mk<R>(ar[k][j], ai[k][j]);
-                        dot[2 * j].fma2(pr[k][j], ar[k][j]);
-                        dot[2 * j].fma2(-pim[k][j], ai[k][j]);
-                        dot[2 * j + 1].fma2(pr[k][j], ai[k][j]);
-                        dot[2 * j + 1].fma2(pim[k][j], ar[k][j]);
+                        ok[(size_t)j * ld] = acc[k][j];
+                        dot[2 * j].fma2(pv[k][j].x, acc[k][j].x);
+                        dot[2 * j].fma2(-pv[k][j].y, acc[k][j].y);
+                        dot[2 * j + 1].fma2(pv[k][j].x, acc[k][j].y);
+                        dot[2 * j + 1].fma2(pv[k][j].y, acc[k][j].x);
                     }
                 } else if constexpr (MIX) {
                     // mixed mode: R = hi + lo, mu_j = R_j^T W_j in double-float
 #pragma unroll
                     for (int j = 0; j < B; ++j) {
-                        ok[(size_t)j * ld] = mk<R>(ar[k][j], ai[k][j]);
+                        ok[(size_t)j * ld] = acc[k][j];
                         const float2 lo =
                             reinterpret_cast<const float2 *>(ea.lo)[tofs + eofs(k) + (size_t)j * ld];
-                        dot[2 * j].fma_hl(pr[k][j], lo.x, ar[k][j]);
-                        dot[2 * j].fma_hl(-pim[k][j], -lo.y, ai[k][j]);
-                        dot[2 * j + 1].fma_hl(pr[k][j], lo.x, ai[k][j]);
-                        dot[2 * j + 1].fma_hl(pim[k][j], lo.y, ar[k][j]);
+                        dot[2 * j].fma_hl(pv[k][j].x, lo.x, acc[k][j].x);
+                        dot[2 * j].fma_hl(-pv[k][j].y, -lo.y, acc[k][j].y);
+                        dot[2 * j + 1].fma_hl(pv[k][j].x, lo.x, acc[k][j].y);
+                        dot[2 * j + 1].fma_hl(pv[k][j].y, lo.y, acc[k][j].x);
                     }
                 }
             }
@@ -356,43 +354,57 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
 // part collects the rounding errors (renormalised when stored). One column
 // per launch, E = 2^LE amplitudes per thread, same tiling, groups and
 // pipeline as the kernel above.
-__device__ __forceinline__ void df_acc(float &h, float &l, float ch, float cl, float ph, float pl) {
-    const float p = ch * ph;
-    float e = fmaf(ch, ph, -p);
-    e = fmaf(ch, pl, e);
-    e = fmaf(cl, ph, e);
-    const float t = h + p;
-    const float bb = t - h;
-    l += ((h - (t - bb)) + (p - bb)) + e;
+// The real and imaginary components take the same operations with the same
+// coefficient, so every step runs on float pairs (re, im) as one packed
+// f32x2 instruction (sm_100 and later). No step negates an operand: a - b is
+// formed as fma(b, -1, a) (the same rounding as the subtraction) and the
+// product's error term from the negated coefficient -c_hi, so each complex
+// term costs 12 packed instructions. h, l: the (re, im) hi and lo parts of
+// the accumulator.
+__device__ __forceinline__ float2 m1x2() { return make_float2(-1.f, -1.f); }
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __ffma2_rn(b, m1x2(), a); }   // a - b
+// acc += c p, c = ch + cl, p = ph + pl; nch = -ch, ncl = -cl:
+//   p_hh = ch ph;  en = -(ch ph - p_hh) - ch pl - cl ph  (exact first step)
+//   t = h + p_hh, Knuth two-sum error into l together with -en
+__device__ __forceinline__ void df_acc2(float2 &h, float2 &l, float2 ch, float2 nch, float2 ncl, float2 ph, float2 pl) {
+    const float2 p = __fmul2_rn(ch, ph);
+    float2 en = __ffma2_rn(nch, ph, p);
+    en = __ffma2_rn(nch, pl, en);
+    en = __ffma2_rn(ncl, ph, en);
+    const float2 t = __fadd2_rn(h, p);
+    const float2 bb = fsub2(t, h);
+    const float2 s = __fadd2_rn(fsub2(h, fsub2(t, bb)), fsub2(p, bb));
+    l = __fadd2_rn(l, fsub2(s, en));
     h = t;
 }
-__device__ __forceinline__ void df_add_to(float &h, float &l, float ph, float pl) {
-    const float t = h + ph;
-    const float bb = t - h;
-    l += ((h - (t - bb)) + (ph - bb)) + pl;
+__device__ __forceinline__ void df_add_to2(float2 &h, float2 &l, float2 ph, float2 pl) {
+    const float2 t = __fadd2_rn(h, ph);
+    const float2 bb = fsub2(t, h);
+    l = __fadd2_rn(l, __fadd2_rn(__fadd2_rn(fsub2(h, fsub2(t, bb)), fsub2(ph, bb)), pl));
     h = t;
 }
 
+// coefficient pairs of one bond for one thread: hi, -hi, -lo of the
+// coefficient at register parity 0 (s) and 1 (f)
+struct DfCoef {
+    float2 sh, snh, snl, fh, fnh, fnl;
+};
 template <int LE, int KA, int KB>
-__device__ __forceinline__ void bond_apply_df(float (&arh)[1 << LE], float (&arl)[1 << LE], float (&aih)[1 << LE],
-                                              float (&ail)[1 << LE], const float2 (&ph)[1 << LE],
-                                              const float2 (&pl)[1 << LE], float csh, float csl, float cfh,
-                                              float cfl) {
+__device__ __forceinline__ void bond_apply_df(float2 (&ah)[1 << LE], float2 (&al)[1 << LE], const float2 (&ph)[1 << LE],
+                                              const float2 (&pl)[1 << LE], const DfCoef &c) {
     constexpr int E = 1 << LE;
 #pragma unroll
     for (int k = 0; k < E; ++k) {
         const int kpar = (KA >= 0 ? (k >> KA) & 1 : 0) ^ (KB >= 0 ? (k >> KB) & 1 : 0);
         const int kp = k ^ KMask<KA, KB>::m;
-        const float ch = kpar ? cfh : csh, cl = kpar ? cfl : csl;
-        df_acc(arh[k], arl[k], ch, cl, ph[kp].x, pl[kp].x);
-        df_acc(aih[k], ail[k], ch, cl, ph[kp].y, pl[kp].y);
+        if (kpar) df_acc2(ah[k], al[k], c.fh, c.fnh, c.fnl, ph[kp], pl[kp]);
+        else df_acc2(ah[k], al[k], c.sh, c.snh, c.snl, ph[kp], pl[kp]);
     }
 }
 
 #define FTK_HV_DF_CASE(ID, KA, KB)                                                                   \
     case ID:                                                                                         \
-        if constexpr (KA < LE && KB < LE)                                                            \
-            bond_apply_df<LE, KA, KB>(arh, arl, aih, ail, ph, pl, csh, csl, cfh, cfl);               \
+        if constexpr (KA < LE && KB < LE) bond_apply_df<LE, KA, KB>(ah, al, ph, pl, cf);             \
         break;
 
 // TB > 0: the thread bits of the tile (tile_bits - LE) as a compile-time
@@ -561,10 +573,10 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
             }
         }
         if (act) {
-            float arh[E], arl[E], aih[E], ail[E];
+            float2 ah[E], al[E];   // (re, im) hi and lo parts of the accumulators
             float2 ph[E], pl[E];
 #pragma unroll
-            for (int k = 0; k < E; ++k) { arh[k] = 0.f; arl[k] = 0.f; aih[k] = 0.f; ail[k] = 0.f; }
+            for (int k = 0; k < E; ++k) { ah[k] = make_float2(0.f, 0.f); al[k] = make_float2(0.f, 0.f); }
             int q = 0;
             for (int g = 0; g < pd.n_groups; ++g) {
                 const int tm = pd.grp_tmask[g];
@@ -577,8 +589,10 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
                 const int pt = __popc(t & tm) & 1;
                 for (const int end = pd.grp_end[g]; q < end; ++q) {
                     const float parh = pd.par_f[q], parl = pd.par_lo[q], anth = pd.anti_f[q], antl = pd.anti_lo[q];
-                    const float csh = pt ? anth : parh, csl = pt ? antl : parl;
-                    const float cfh = pt ? parh : anth, cfl = pt ? parl : antl;
+                    const float sh_ = pt ? anth : parh, sl_ = pt ? antl : parl;
+                    const float fh_ = pt ? parh : anth, fl_ = pt ? parl : antl;
+                    const DfCoef cf = {make_float2(sh_, sh_), make_float2(-sh_, -sh_), make_float2(-sl_, -sl_),
+                                       make_float2(fh_, fh_), make_float2(-fh_, -fh_), make_float2(-fl_, -fl_)};
                     switch (pd.bcase[q]) {
                         FTK_HV_DF_CASE(0, -1, -1)
                         FTK_HV_DF_CASE(1, 0, -1)
@@ -597,35 +611,32 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
             }
             // own amplitudes (last group): diagonal
 #pragma unroll
-            for (int k = 0; k < E; ++k) {
-                df_acc(arh[k], arl[k], dgh[k], dgl[k], ph[k].x, pl[k].x);
-                df_acc(aih[k], ail[k], dgh[k], dgl[k], ph[k].y, pl[k].y);
-            }
+            for (int k = 0; k < E; ++k)
+                df_acc2(ah[k], al[k], make_float2(dgh[k], dgh[k]), make_float2(-dgh[k], -dgh[k]),
+                        make_float2(-dgl[k], -dgl[k]), ph[k], pl[k]);
             if (!first) {
                 if (more) cp_async_wait<1>(); else cp_async_wait<0>();
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     const float4 v4 = pb[t + T * k];
-                    const float2 h = make_float2(v4.x, v4.y), l = make_float2(v4.z, v4.w);
-                    df_add_to(arh[k], arl[k], h.x, l.x);
-                    df_add_to(aih[k], ail[k], h.y, l.y);
+                    df_add_to2(ah[k], al[k], make_float2(v4.x, v4.y), make_float2(v4.z, v4.w));
                 }
             }
             float2 *o = out + tofs;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 // renormalise (fast two-sum) and store hi, lo
-                const float rh = arh[k] + arl[k], rl = arl[k] - (rh - arh[k]);
-                const float ih = aih[k] + ail[k], il = ail[k] - (ih - aih[k]);
+                const float2 hh = __fadd2_rn(ah[k], al[k]);
+                const float2 ll = fsub2(al[k], fsub2(hh, ah[k]));
                 float2 *ok = o + eofs(k);
-                ok[0] = make_float2(rh, ih);
-                ok[lo] = make_float2(rl, il);
+                ok[0] = hh;
+                ok[lo] = ll;
                 if (EPI == EPI_COCG && pd.last) {
                     // mu = r^T w (bilinear) in double-float from hi + lo
-                    dot[0].fma_pair(ph[k].x, pl[k].x, rh, rl);
-                    dot[0].fma_pair(-ph[k].y, -pl[k].y, ih, il);
-                    dot[1].fma_pair(ph[k].x, pl[k].x, ih, il);
-                    dot[1].fma_pair(ph[k].y, pl[k].y, rh, rl);
+                    dot[0].fma_pair(ph[k].x, pl[k].x, hh.x, ll.x);
+                    dot[0].fma_pair(-ph[k].y, -pl[k].y, hh.y, ll.y);
+                    dot[1].fma_pair(ph[k].x, pl[k].x, hh.y, ll.y);
+                    dot[1].fma_pair(ph[k].y, pl[k].y, hh.x, ll.x);
                 }
             }
         }

@@ -289,12 +289,14 @@ class Server:
 
 
 # ------------------------------------------------------------------ stream
-def poisson_stream(n_jobs, seed=1234, rate=2.0, sizes=(12, 16, 18, 20), precisions=("fp64", "df")):
+def poisson_stream(n_jobs, seed=1234, rate=2.0, sizes=(12, 16, 18, 20), precisions=("fp64", "df"), n_steps=21,
+                   temps=(0.005, 2.0), omega_counts=(256, 512, 1024), etas=(0.01, 0.02), max_probes=2):
     """Seeded synthetic job stream of the serving workload, scaled to one GPU
     and minutes: Poisson arrivals at `rate` jobs/s; per job a cluster size from
     `sizes`, K = -1, J ~ U[-0.3, 0.3], one or two probes (random spin component
-    and momentum), eta in {0.01, 0.02}, 16-64 temperatures in [0.005, 2],
-    256-1024 shifts on [-3, 3], a precision from `precisions`. Returns a list of
+    and momentum; at most max_probes), eta from etas, 16-64 temperatures in [temps[0],
+    temps[1]], shifts on [-3, 3] (a count from omega_counts), a precision from
+    `precisions`, n_steps mTPQ steps with shells every 20. Returns a list of
     (arrival offset in s, JobSpec)."""
     rng = np.random.default_rng(seed)
     t, out = 0.0, []
@@ -302,13 +304,14 @@ def poisson_stream(n_jobs, seed=1234, rate=2.0, sizes=(12, 16, 18, 20), precisio
         t += rng.exponential(1.0 / rate)
         n = int(rng.choice(sizes))
         n_mom = n // 2
-        probes = [(int(rng.integers(0, 3)), int(rng.integers(0, n_mom))) for _ in range(int(rng.integers(1, 3)))]
+        probes = [(int(rng.integers(0, 3)), int(rng.integers(0, n_mom)))
+                  for _ in range(int(rng.integers(1, max_probes + 1)))]
         n_t = int(rng.integers(16, 65))
         spec = JobSpec(n_sites=n, K=-1.0, J=float(rng.uniform(-0.3, 0.3)), seed=int(rng.integers(1, 2**31)),
-                       n_steps=21, save_every=20, probes=probes,
-                       omega=(-3.0, 3.0, int(rng.choice([256, 512, 1024]))),
-                       eta=float(rng.choice([0.01, 0.02])),
-                       temps=list(np.geomspace(0.005, 2.0, n_t)), precision=str(rng.choice(precisions)),
+                       n_steps=n_steps, save_every=20, probes=probes,
+                       omega=(-3.0, 3.0, int(rng.choice(list(omega_counts)))),
+                       eta=float(rng.choice(list(etas))),
+                       temps=list(np.geomspace(temps[0], temps[1], n_t)), precision=str(rng.choice(precisions)),
                        tol=1e-4, max_iter=12000, block=4)
         out.append((t, spec))
     return out
