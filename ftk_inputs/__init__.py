@@ -2,5 +2,5 @@
 
 Holds geometry and random inputs only, none of the method's arithmetic.
 """
-from .lattice import Cluster, honeycomb, named, relabel, GAMMA_X, GAMMA_Y, GAMMA_Z  # noqa: F401
+from .lattice import Cluster, honeycomb, named, relabel, translations, characters, GAMMA_X, GAMMA_Y, GAMMA_Z  # noqa: F401
 from .states import random_state, random_vectors, omega_grid, log_temperatures  # noqa: F401

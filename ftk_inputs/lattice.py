@@ -183,6 +183,48 @@ def relabel(cl: Cluster, perm) -> Cluster:
                    cl.supercell.copy(), cl.name, perm)
 
 
+def translations(cl: Cluster):
+    """The translation group of the torus as site permutations.
+
+    Returns (perms int32 [n_cells, N], vectors float64 [n_cells, 2]): element g
+    moves site l to site perms[g, l], the site at R_l + a_g modulo the
+    supercell (a_g = vectors[g], a lattice vector); element 0 is the
+    identity. Works from the positions, so it holds for relabelled clusters
+    too. Geometry only: a momentum sector is chosen by the caller through
+    the characters exp(-i Q . a_g)."""
+    m = cl.supercell
+    reps, reduce, det = _cells(m)
+    a = np.stack([A1, A2])                 # rows a_1, a_2
+    ainv = np.linalg.inv(a)
+    n = cl.n_sites
+    key = {}
+    for l in range(n):
+        for sub, off in ((0, np.zeros(2)), (1, D_Z)):
+            f = (cl.pos[l] - off) @ ainv
+            if np.allclose(f, np.round(f), atol=1e-9):
+                cell = reduce(tuple(int(v) for v in np.round(f)))
+                key[(sub, cell)] = l
+                break
+        else:
+            raise RuntimeError("site position is not on the honeycomb lattice")
+    site_key = {l: k for k, l in key.items()}
+    cells = sorted(reps, key=lambda t: (t != (0, 0), t[1], t[0]))   # identity first
+    perms, vecs = [], []
+    for t1, t2 in cells:
+        pm = np.zeros(n, dtype=np.int32)
+        for l in range(n):
+            sub, (n1, n2) = site_key[l]
+            pm[l] = key[(sub, reduce((n1 + t1, n2 + t2)))]
+        perms.append(pm)
+        vecs.append(t1 * A1 + t2 * A2)
+    return np.array(perms, dtype=np.int32), np.array(vecs)
+
+
+def characters(vectors, q):
+    """exp(-i q . a_g) for the translation vectors a_g (the sector of momentum q)."""
+    return np.exp(-1j * (np.asarray(vectors) @ np.asarray(q, dtype=np.float64)))
+
+
 # Named clusters used by the workloads (cells x 2 sites).
 NAMED = {
     2: (1, 1),

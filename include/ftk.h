@@ -276,6 +276,109 @@ ftk_status ftk_filter_spectrum(ftk_ctx *ctx, const double *G, int32_t n_shell, i
 ftk_status ftk_spectrum(ftk_ctx *ctx, const double *G, int32_t n_shell, int32_t n_omega,
                         const double *T, int32_t n_T, double *S_out, int32_t *trunc_out);
 
+/* ftk_spectrum with the mTPQ statistics given by the caller instead of the
+ * context's sequence (the same reading R1 of Eq. B1): u[k] = u_k, logQ[k] =
+ * log Q_k for k < n_steps (host), shells s at steps s save_every, l = ell.
+ * For statistics merged from momentum sectors (ftk_sector_combine) or kept
+ * from an earlier TPQ sequence. Requires l > u_k and (n_shell - 1) save_every
+ * < n_steps <= 262144. Other arguments and outputs as ftk_spectrum. */
+ftk_status ftk_spectrum_ex(ftk_ctx *ctx, const double *G, int32_t n_shell, int32_t n_omega, const double *T,
+                           int32_t n_T, const double *u, const double *logQ, int32_t n_steps, int32_t save_every,
+                           double ell, double *S_out, int32_t *trunc_out);
+
+/* ---------------------------------------------------------------------------
+ * Momentum sectors (translation symmetry). The paper works in the full basis
+ * (Sec. V); a sector reduces the dimension by the number of translations
+ * (N/2) for larger clusters. A group of site permutations g (element 0 the
+ * identity; each must map the bond list of the context to itself) acts on
+ * basis states, bit g(l) of g.x = bit l of x, and commutes with H. A sector
+ * is a unitary one-dimensional character chi of the group (for the torus
+ * translation by a_g at momentum Q: chi(g) = exp(-i Q.a_g)); its basis
+ * vectors are |r>_chi = sqrt(o_r) P|r>, P = (1/|G|) sum_g chi(g)^* g, for the
+ * orbit representatives r (smallest integer of the orbit, o_r its size) on
+ * whose stabiliser chi is 1. A sector vector holds dim complex amplitudes
+ * (FP64 (re, im)) in ascending order of r.
+ * The sector owns its device memory (allocated by ftk_sector_create): 4 B per
+ * full-basis state for the state -> (orbit, element) table, the orbit list,
+ * and n_slots sector vectors; 9 B per full-basis state of temporary memory
+ * during creation. Work runs on the context's stream.
+ * ------------------------------------------------------------------------- */
+typedef struct ftk_sector ftk_sector;
+
+/* perms: host [n_g][n_sites] (site l -> perms[g][l]), 1 <= n_g <= 32; chi: host
+ * [n_g][2] (re, im). n_slots: sector vectors kept (1..64). *dim_out
+ * receives the sector dimension. FTK_EINVAL if the permutations do not form
+ * a group preserving the bonds, or chi is not a character of it. */
+ftk_status ftk_sector_create(ftk_ctx *ctx, const int32_t *perms, int32_t n_g, const double *chi, int32_t n_slots,
+                             ftk_sector **out, int64_t *dim_out);
+void ftk_sector_destroy(ftk_sector *sector);
+
+/* Dimension, number of orbits of the group, and (host [dim], may be NULL) the
+ * representative of every sector basis vector. Synchronises. */
+ftk_status ftk_sector_info(const ftk_sector *sector, int64_t *dim, int32_t *n_orbits, uint32_t *reps_host);
+
+/* Copy a sector vector in (host or device) / out (host). Synchronise. */
+ftk_status ftk_sector_set(ftk_sector *sector, int32_t slot, const double *v, int32_t is_device);
+ftk_status ftk_sector_get(ftk_sector *sector, int32_t slot, double *host_out);
+
+/* Components of a full-basis state in the sector: slot[r] = <r|_chi psi =
+ * (sqrt(o_r)/|G|) sum_h chi(h)^* psi[h^{-1}.r]. psi: 2^N complex (re, im)
+ * doubles, host (is_device = 0) or device. Synchronises. */
+ftk_status ftk_sector_project(ftk_sector *sector, const double *psi_full, int32_t is_device, int32_t slot);
+
+/* slot_out = H_chi slot_in (the sector block of the Kitaev-Heisenberg H of the
+ * context, Sec. V.A; a gather over the bonds of each representative with the
+ * character phases). Asynchronous. */
+ftk_status ftk_sector_hv(ftk_sector *sector, int32_t slot_in, int32_t slot_out);
+
+/* mTPQ iteration in the sector (Appendix A): the state in slot_state is
+ * normalised (log of its norm to *lognorm0_out, may be NULL), then n_steps
+ * times psi_{k+1} = (l - H/N) psi_k / q_k with slot_work as scratch; psi_k is
+ * copied to slot first_save_slot + k / save_every when k % save_every == 0.
+ * Host outputs (length n_steps, may be NULL): u_out[k] = <psi_k|H|psi_k>/N,
+ * logq_out[k] = log of the product of q below k. Sector parts of one full
+ * state are merged by ftk_sector_combine. ell >= l_min as ftk_tpq_init.
+ * Synchronises. */
+ftk_status ftk_sector_tpq(ftk_sector *sector, int32_t slot_state, int32_t slot_work, double ell, int32_t n_steps,
+                          int32_t save_every, int32_t first_save_slot, double *u_out, double *logq_out,
+                          double *lognorm0_out);
+
+/* lambda = S^z_q psi (Sec. V) from sector src to sector dst, which must be
+ * src's sector shifted by q (chi_dst(g) = chi_src(g) exp(-i q.a_g), checked
+ * on the translation of site 0): S^z_q keeps the representative,
+ * lambda[r] = f_q(r) psi[r], f_q(r) = N^{-1/2} sum_l e^{i q.R_l} s_l(r)/2.
+ * Synchronises. */
+ftk_status ftk_sector_apply_sz(ftk_sector *src, int32_t slot_src, ftk_sector *dst, int32_t slot_dst,
+                               const double q[2]);
+
+/* G(z_s) = <lambda|(z_s - H_chi)^{-1}|lambda> for lambda in slot and the
+ * complex shifts z_s (host [n_shift][2]): the Hermitian Lanczos process on
+ * H_chi (a sector block is complex Hermitian, so the bilinear COCG does not
+ * apply) with the shifted recurrences of the LDL^T factors of z - T_j,
+ *   d_j = z - a_j - b_j^2/d_{j-1},  y_j = y_{j-1} b_j/d_{j-1},
+ *   G_j = |lambda|^2 sum_i y_i^2/d_i;
+ * a shift stops once |b_{j+1} y_j/d_j| <= tol (its residual relative to
+ * |lambda|, the criterion of ftk_shifted_cocg). The three slots after `slot`
+ * (cyclically; n_slots >= 4) are overwritten. G_out: host [n_shift][2];
+ * iters_out: Lanczos steps. FTK_ENOCONV at max_iter (G written).
+ * Synchronises. */
+ftk_status ftk_sector_green(ftk_sector *sector, int32_t slot, const double *shifts, int32_t n_shift, double tol,
+                            int32_t max_iter, double *G_out, int32_t *iters_out);
+
+/* Merge the sector parts of one full-space mTPQ sequence (host arithmetic):
+ * with a_s[k] = lognorm0[s] + logq[s][k], the full statistics
+ *   logQ_out[k] = (1/2) log sum_s e^{2 a_s[k]} - (1/2) log sum_s e^{2 lognorm0[s]},
+ *   u_out[k]    = sum_s e^{2 a_s[k]} u[s][k] / sum_s e^{2 a_s[k]},
+ * and the Green's functions of the normalised full shells
+ *   G_out[i] = sum_s e^{2 a_s[k_i]} G[s][i] / sum_s e^{2 a_s[k_i]},  k_i = shell_steps[i],
+ * from each sector's G of its normalised shell (S^z_q maps each sector to
+ * one sector, so the sector blocks of the resolvent add). Arrays host:
+ * lognorm0 [n_sec], logq and u [n_sec][n_steps], G [n_sec][n_shell][n_omega][2],
+ * outputs u_out, logQ_out [n_steps], G_out [n_shell][n_omega][2]. */
+ftk_status ftk_sector_combine(int32_t n_sec, int32_t n_steps, const double *lognorm0, const double *logq,
+                              const double *u, int32_t n_shell, const int32_t *shell_steps, int32_t n_omega,
+                              const double *G, double *u_out, double *logQ_out, double *G_out);
+
 /* out = H v for n_rhs vectors stored one after the other (layout
  * [n_rhs][2^N] complex in the matvec precision: FP64 for FTK_FP64, FP32 for
  * FTK_FP32 and FTK_MIXED; vector j at offset j 2^N; for FTK_DF the FP32 hi

@@ -20,6 +20,9 @@ Parts:
               probability distribution and Green's function (Sec. II.C-D).
   cocg3.py    shifted COCG in the three-term (residual-only) form of the
               CUDA path, with optional seed switching.
+  sector.py   momentum sectors of the translation group: the sector basis
+              from its definition, the sector block of H, projection and
+              embedding.
 
 Every function is pinned by -m "not gpu" tests (tests/test_oracle_*.py)
 against closed forms, brute force, invariants and published test vectors.

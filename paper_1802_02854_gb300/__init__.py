@@ -30,7 +30,10 @@ EXPORTS = ["ftk_footprint", "ftk_create", "ftk_bind_workspace", "ftk_tpq_init", 
            "ftk_tpq_step", "ftk_shells", "ftk_apply_op", "ftk_set_probe", "ftk_shifted_cocg",
            "ftk_spectrum", "ftk_hv", "ftk_get_vector", "ftk_plan_info", "ftk_launch_count",
            "ftk_last_error", "ftk_destroy", "ftk_tpq_step_noalloc", "ftk_suggest_order", "ftk_autotune", "ftk_set_relax",
-           "ftk_shifted_cocg_ex", "ftk_ctpq", "ftk_filter_footprint", "ftk_filter_shells", "ftk_filter_spectrum"]
+           "ftk_shifted_cocg_ex", "ftk_ctpq", "ftk_filter_footprint", "ftk_filter_shells", "ftk_filter_spectrum",
+           "ftk_spectrum_ex", "ftk_sector_create", "ftk_sector_destroy", "ftk_sector_info", "ftk_sector_set",
+           "ftk_sector_get", "ftk_sector_project", "ftk_sector_hv", "ftk_sector_tpq", "ftk_sector_apply_sz",
+           "ftk_sector_green", "ftk_sector_combine"]
 
 
 class FtkError(RuntimeError):
@@ -102,8 +105,22 @@ def lib() -> C.CDLL:
     L.ftk_filter_footprint.restype = C.c_size_t
     L.ftk_filter_shells.argtypes = [vp, i32, dbl, dbl, i32, i32, dbl, i32, vp, C.c_size_t, i32, pd, pi]
     L.ftk_filter_spectrum.argtypes = [vp, pd, i32, i32, pd, pd, dbl, dbl, pd, i32, pd, pd]
+    L.ftk_spectrum_ex.argtypes = [vp, pd, i32, i32, pd, i32, pd, pd, i32, i32, dbl, pd, pi]
+    L.ftk_sector_create.argtypes = [vp, pi, i32, pd, i32, C.POINTER(vp), C.POINTER(i64)]
+    L.ftk_sector_destroy.argtypes = [vp]
+    L.ftk_sector_destroy.restype = None
+    L.ftk_sector_info.argtypes = [vp, C.POINTER(i64), pi, C.POINTER(C.c_uint32)]
+    L.ftk_sector_set.argtypes = [vp, i32, vp, i32]
+    L.ftk_sector_get.argtypes = [vp, i32, pd]
+    L.ftk_sector_project.argtypes = [vp, vp, i32, i32]
+    L.ftk_sector_hv.argtypes = [vp, i32, i32]
+    L.ftk_sector_tpq.argtypes = [vp, i32, i32, dbl, i32, i32, i32, pd, pd, pd]
+    L.ftk_sector_apply_sz.argtypes = [vp, i32, vp, i32, pd]
+    L.ftk_sector_green.argtypes = [vp, i32, pd, i32, dbl, i32, pd, pi]
+    L.ftk_sector_combine.argtypes = [i32, i32, pd, pd, pd, i32, pi, i32, pd, pd, pd, pd]
     for name in EXPORTS:
-        if name not in ("ftk_footprint", "ftk_launch_count", "ftk_last_error", "ftk_destroy", "ftk_filter_footprint"):
+        if name not in ("ftk_footprint", "ftk_launch_count", "ftk_last_error", "ftk_destroy", "ftk_filter_footprint",
+                        "ftk_sector_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -262,6 +279,120 @@ def ftk_filter_spectrum(ctx, G, energy, norm2, beta, eps, T):
     return S, P
 
 
+def ftk_spectrum_ex(ctx, G, T, u, logQ, save_every, ell):
+    """R1 reweighting with caller statistics; returns (S [n_T, n_omega], trunc [n_T])."""
+    G = np.ascontiguousarray(G, dtype=np.complex128)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    lq = np.ascontiguousarray(logQ, dtype=np.float64)
+    S = np.zeros((len(T), G.shape[1]))
+    tr = np.zeros(len(T), dtype=np.int32)
+    _check(ctx, lib().ftk_spectrum_ex(ctx, G.ctypes.data_as(C.POINTER(C.c_double)), G.shape[0], G.shape[1], _dp(T),
+                                      len(T), _dp(u), _dp(lq), len(u), int(save_every), float(ell), _dp(S), _ip(tr)),
+           (FTK_OK, FTK_ETRUNC))
+    return S, tr
+
+
+def ftk_sector_combine(lognorm0, logq, u, shell_steps=None, G=None):
+    """Merge sector statistics (and per-sector shell Green's functions
+    G [n_sec, n_shell, n_omega]); returns (u, logQ, G or None)."""
+    ln = np.ascontiguousarray(lognorm0, dtype=np.float64)
+    lq = np.ascontiguousarray(logq, dtype=np.float64)
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    n_sec, n_steps = lq.shape
+    uo = np.zeros(n_steps)
+    lo = np.zeros(n_steps)
+    if G is None:
+        _check(None, lib().ftk_sector_combine(n_sec, n_steps, _dp(ln), _dp(lq), _dp(uu), 0, None, 0, None, _dp(uo),
+                                              _dp(lo), None))
+        return uo, lo, None
+    Gs = np.ascontiguousarray(G, dtype=np.complex128)
+    st = np.ascontiguousarray(shell_steps, dtype=np.int32)
+    Go = np.zeros(Gs.shape[1:], dtype=np.complex128)
+    _check(None, lib().ftk_sector_combine(n_sec, n_steps, _dp(ln), _dp(lq), _dp(uu), Gs.shape[1], _ip(st),
+                                          Gs.shape[2], Gs.ctypes.data_as(C.POINTER(C.c_double)), _dp(uo), _dp(lo),
+                                          Go.ctypes.data_as(C.POINTER(C.c_double))))
+    return uo, lo, Go
+
+
+class Sector:
+    """A momentum sector of a context (translation group perms [n_g, N] and
+    character chi [n_g] complex); owns its device memory."""
+
+    def __init__(self, ctx, perms, chi, n_slots=8):
+        self.ctx = ctx
+        P = np.ascontiguousarray(perms, dtype=np.int32)
+        ch = np.ascontiguousarray(chi, dtype=np.complex128)
+        h = C.c_void_p()
+        d = C.c_int64()
+        _check(ctx.handle, lib().ftk_sector_create(ctx.handle, _ip(P), P.shape[0],
+                                                   ch.ctypes.data_as(C.POINTER(C.c_double)), int(n_slots),
+                                                   C.byref(h), C.byref(d)))
+        self.handle = h.value
+        self.dim = int(d.value)
+        self.n_slots = n_slots
+
+    def info(self):
+        d = C.c_int64()
+        no = C.c_int32()
+        reps = np.zeros(self.dim, dtype=np.uint32)
+        _check(self.ctx.handle, lib().ftk_sector_info(self.handle, C.byref(d), C.byref(no),
+                                                      reps.ctypes.data_as(C.POINTER(C.c_uint32))))
+        return int(d.value), int(no.value), reps
+
+    def set(self, slot, v):
+        a = np.ascontiguousarray(v, dtype=np.complex128)
+        _check(self.ctx.handle, lib().ftk_sector_set(self.handle, int(slot), a.ctypes.data_as(C.c_void_p), 0))
+
+    def get(self, slot):
+        out = np.zeros(self.dim, dtype=np.complex128)
+        _check(self.ctx.handle, lib().ftk_sector_get(self.handle, int(slot), out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def project(self, psi, slot):
+        a = np.ascontiguousarray(psi, dtype=np.complex128)
+        _check(self.ctx.handle, lib().ftk_sector_project(self.handle, a.ctypes.data_as(C.c_void_p), 0, int(slot)))
+
+    def hv(self, slot_in, slot_out):
+        _check(self.ctx.handle, lib().ftk_sector_hv(self.handle, int(slot_in), int(slot_out)))
+        self.ctx.stream.synchronize()
+
+    def tpq(self, slot_state, slot_work, ell, n_steps, save_every, first_save_slot):
+        u = np.zeros(n_steps)
+        lq = np.zeros(n_steps)
+        l0 = C.c_double()
+        _check(self.ctx.handle, lib().ftk_sector_tpq(self.handle, int(slot_state), int(slot_work), float(ell),
+                                                     int(n_steps), int(save_every), int(first_save_slot), _dp(u),
+                                                     _dp(lq), C.byref(l0)))
+        return u, lq, l0.value
+
+    def apply_sz(self, slot_src, dst, slot_dst, q):
+        qq = np.ascontiguousarray(q, dtype=np.float64)
+        _check(self.ctx.handle, lib().ftk_sector_apply_sz(self.handle, int(slot_src), dst.handle, int(slot_dst),
+                                                          _dp(qq)))
+
+    def green(self, slot, shifts, tol=1e-10, max_iter=10000, allow_noconv=False):
+        z = np.ascontiguousarray(shifts, dtype=np.complex128)
+        G = np.zeros(len(z), dtype=np.complex128)
+        it = C.c_int32()
+        ok = (FTK_OK, FTK_ENOCONV) if allow_noconv else (FTK_OK,)
+        _check(self.ctx.handle, lib().ftk_sector_green(self.handle, int(slot), z.ctypes.data_as(C.POINTER(C.c_double)),
+                                                       len(z), float(tol), int(max_iter),
+                                                       G.ctypes.data_as(C.POINTER(C.c_double)), C.byref(it)), ok)
+        return G, it.value
+
+    def close(self):
+        if self.handle:
+            lib().ftk_sector_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def ftk_spectrum(ctx, G, T):
     """G: complex128 [n_shell, n_omega]; returns (S [n_T, n_omega], trunc [n_T])."""
     G = np.ascontiguousarray(G, dtype=np.complex128)
@@ -393,6 +524,9 @@ class Context:
 
     def spectrum(self, G, T):
         return ftk_spectrum(self.handle, G, T)
+
+    def spectrum_ex(self, G, T, u, logQ, save_every, ell):
+        return ftk_spectrum_ex(self.handle, G, T, u, logQ, save_every, ell)
 
     def shifted_cocg_ex(self, slots, shifts, tol=1e-4, max_iter=10000, proj_slots=None, seed_index=-1,
                         seed_switch=False, allow_noconv=False):

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libftk.so")
-SOURCES = ["ftk_api.cu", "ftk_kernels.cu", "ftk_hv.cu", "ftk_noalloc.cu"]
+SOURCES = ["ftk_api.cu", "ftk_kernels.cu", "ftk_hv.cu", "ftk_noalloc.cu", "ftk_sector.cu"]
 HEADERS = ["ftk_common.cuh", "ftk_kernels.h", "ftk_plan.h", "ftk_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "128"]

@@ -268,6 +268,23 @@ ftk_status check_ell(ftk_ctx *ctx, double ell) {
 
 }  // namespace
 
+// Hamiltonian and stream of a context for the momentum-sector code.
+bool ftk::ctx_hamiltonian(ftk_ctx *c, CtxHam *h) {
+    if (!c) return false;
+    h->n = c->n;
+    h->nb = c->nb;
+    h->bonds = reinterpret_cast<const int *>(c->bonds.data());
+    h->K = c->K;
+    h->J = c->J;
+    h->ell_min = c->ell_min;
+    h->pos = c->pos.data();
+    h->stream = c->stream;
+    h->n_sm = c->n_sm;
+    h->launches = &c->launches;
+    h->err = &c->err;
+    return true;
+}
+
 extern "C" {
 
 size_t ftk_footprint(int32_t n_sites, int32_t n_saved, int32_t max_rhs, int32_t precision) {
@@ -1301,6 +1318,62 @@ ftk_status ftk_spectrum(ftk_ctx *ctx, const double *Gh, int32_t n_shell, int32_t
     sp.trunc = trb;
     LAUNCH(launch_spectrum(sp, n_T, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(S_out, sb, sizeof(double) * n_T * n_omega, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<int> tr(n_T);
+    CK(cudaMemcpyAsync(tr.data(), trb, sizeof(int) * n_T, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int any = 0;
+    for (int t = 0; t < n_T; ++t) {
+        if (trunc_out) trunc_out[t] = tr[t];
+        any |= tr[t];
+    }
+    return any ? FTK_ETRUNC : FTK_OK;
+}
+
+ftk_status ftk_spectrum_ex(ftk_ctx *ctx, const double *Gh, int32_t n_shell, int32_t n_omega, const double *T,
+                           int32_t n_T, const double *u, const double *logQ, int32_t n_steps, int32_t save_every,
+                           double ell, double *S_out, int32_t *trunc_out) {
+    ftk_status s = check_ready(ctx);
+    if (s) return s;
+    if (!Gh || !T || !S_out || !u || !logQ || n_shell < 1 || n_shell > 1024 || n_omega < 1 ||
+        n_omega > FTK_MAX_OMEGA || n_T < 1 || n_T > 1024 || n_steps < 1 || save_every < 1 ||
+        (size_t)n_steps * 16 > kPartialsBytes || (n_shell - 1) * save_every >= n_steps || !std::isfinite(ell))
+        return fail(ctx, FTK_EINVAL, "bad spectrum arguments");
+    for (int t = 0; t < n_T; ++t)
+        if (!(T[t] > 0)) return fail(ctx, FTK_EINVAL, "temperatures must be positive");
+    for (int k = 0; k < n_steps; ++k)
+        if (!(ell - u[k] > 0) || !std::isfinite(logQ[k])) return fail(ctx, FTK_EINVAL, "need l > u_k and finite log Q_k");
+    double *gb = (double *)wsp(ctx, ctx->L.gbuf);
+    double *tb = (double *)wsp(ctx, ctx->L.tbuf);
+    double *ub = (double *)wsp(ctx, ctx->L.partials), *qb = ub + n_steps;
+    const size_t s_need = size_t(n_T) * n_omega * 8 + n_T * 4 + 16;
+    const size_t g_used = align_up(size_t(16) * n_shell * n_omega);
+    double *sb = (double *)wsp(ctx, ctx->L.kry[0]);
+    if (ctx->L.vec_bytes * ctx->max_rhs < s_need) {
+        if (g_used + s_need > ctx->L.tbuf - ctx->L.gbuf)
+            return fail(ctx, FTK_ENOMEM, "no workspace region large enough to stage the spectrum");
+        sb = (double *)wsp(ctx, ctx->L.gbuf + g_used);
+    }
+    int *trb = (int *)(sb + size_t(n_T) * n_omega);
+    CK(cudaMemcpyAsync(gb, Gh, size_t(16) * n_shell * n_omega, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(tb, T, sizeof(double) * n_T, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ub, u, sizeof(double) * n_steps, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(qb, logQ, sizeof(double) * n_steps, cudaMemcpyHostToDevice, ctx->stream));
+    SpecArgs sp{};
+    sp.n_sites_i = ctx->n;
+    sp.n_sites = ctx->n;
+    sp.ell = ell;
+    sp.n_steps = n_steps;
+    sp.save_every = save_every;
+    sp.n_shell = n_shell;
+    sp.n_omega = n_omega;
+    sp.u = ub;
+    sp.logq = qb;
+    sp.G = gb;
+    sp.T = tb;
+    sp.S = sb;
+    sp.trunc = trb;
+    LAUNCH(launch_spectrum(sp, n_T, ctx->stream));
     CK(cudaMemcpyAsync(S_out, sb, sizeof(double) * n_T * n_omega, cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<int> tr(n_T);
     CK(cudaMemcpyAsync(tr.data(), trb, sizeof(int) * n_T, cudaMemcpyDeviceToHost, ctx->stream));

@@ -2,6 +2,8 @@
 #pragma once
 #include "ftk_common.cuh"
 
+#include <string>
+
 namespace ftk {
 
 enum { EPI_PLAIN = 0, EPI_TPQ = 1, EPI_COCG = 2, EPI_COCG_MIXED = 3, EPI_TAYLOR = 4 };
@@ -196,6 +198,21 @@ struct SpecArgs {
 
 cudaError_t init_kernel_attributes();
 void set_thread_error(const char *msg);   // message for ftk_last_error(NULL)
+// What the momentum-sector code reads from a context.
+struct CtxHam {
+    int n, nb;
+    const int *bonds;        // [nb][3]: i, j, gamma
+    double K, J, ell_min;
+    const double *pos;       // [n][2]
+    cudaStream_t stream;
+    int n_sm;
+    int64_t *launches;       // the context's launch counter
+    std::string *err;        // the context's last error message
+};
+}  // namespace ftk
+struct ftk_ctx;
+namespace ftk {
+bool ctx_hamiltonian(ftk_ctx *c, CtxHam *h);
 // H.V pass (ftk_hv.cu). A planned pass is laid out once for the kernel's
 // thread layout and a column chunk width cols <= hv_max_b(prec)
 // (hv_layout_pass); a launch of B right-hand sides then runs B / cols column
