@@ -75,7 +75,7 @@ FP64_PEAK_TFLOPS = 1.25
 # dram__bytes_read.sum + dram__bytes_write.sum summed over the three passes of
 # the 24-site plan with 2^12-amplitude tiles (one column, --hv-only); valid
 # for that plan of the current kernel only
-DF_HV_DRAM_BYTES = None
+DF_HV_DRAM_BYTES = 1999.1e6     # 1342.5 MB read + 656.6 MB written
 DF_HV_DRAM_PLAN = (24, 3, 12)    # (sites, passes, tile bits) the counters were taken on
 
 
@@ -391,6 +391,20 @@ def run_gpu(args):
                           "frac": round(2 * dim * 8 / t_hv1 / 1e9 / peak, 4), "peak": peak,
                           "peak_kind": peak_kind, "passes": p1[0]}
 
+    # the batched configuration's knob: FP64 blocked H.V time per column
+    # against the block width (tile size and column chunk autotuned per width)
+    blocked = {"B": [], "us_per_column": [], "plan": []}
+    if not args.no_block_sweep:
+        for B in (1, 4, 8, 16, 32):
+            cb = ftk.Context(cl, K_COUPLING, J_COUPLING, "fp64", max_rhs=B)
+            tb_, cols_, _ = cb.autotune(B, 0)
+            t_b = time_hv(cb, torch, B, torch.complex128, reps=3)
+            blocked["B"].append(B)
+            blocked["us_per_column"].append(round(t_b * 1e6 / B, 1))
+            blocked["plan"].append([tb_, cols_, cb.plan_info()[0]])
+            cb.close()
+    roof["hv_fp64_blocked"] = blocked
+
     # plain FP64 single-vector FTKomega on the same GPU and input (timed step
     # 0's state), and a converged FP64 reference (tol 1e-9) for the errors
     ctx64 = ftk.Context(cl, K_COUPLING, J_COUPLING, "fp64", max_rhs=n_rhs, n_saved=N_SHELLS)
@@ -522,6 +536,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--no-block-sweep", action="store_true", help="skip the FP64 block-width sweep")
     ap.add_argument("--hv-only", action="store_true", help="only a few H.V launches (profiling)")
     ap.add_argument("--hv-sites", type=int, default=N_SITES)
     ap.add_argument("--hv-prec", default="fp32", choices=["fp64", "fp32", "df"])

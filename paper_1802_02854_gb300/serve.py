@@ -60,6 +60,19 @@ class JobSpec:
         from . import PRECISIONS, ftk_footprint
         return ftk_footprint(self.n_sites, self.n_shells, self.block, PRECISIONS[self.precision]) + CTX_OVERHEAD_BYTES
 
+    @property
+    def n_rhs(self):
+        """Right-hand sides of the job: every probe on every saved shell."""
+        return len(self.probes) * self.n_shells
+
+    def pack_key(self):
+        """Jobs with equal keys can share one blocked solve: the same cluster
+        and Hamiltonian, precision, shift grid, eta and stopping rule (the
+        seeds, probes and temperatures may differ)."""
+        cl = ("named", self.n_sites) if self.cluster is None else ("cluster", id(self.cluster))
+        return (cl, float(self.K), float(self.J), self.ell, self.precision, tuple(self.omega), float(self.eta),
+                float(self.tol), int(self.max_iter))
+
 
 @dataclass
 class JobResult:
@@ -136,18 +149,85 @@ def run_job(spec: JobSpec, stream=None):
         ctx.close()
 
 
+def run_pack(specs, stream=None):
+    """Run jobs with equal pack keys as one: one context, each job's mTPQ
+    sequence and probes in turn (its probes are built before the next job's
+    sequence overwrites the shells), ONE blocked shifted solve over all their
+    right-hand sides, and each job's spectra reweighted with its own mTPQ
+    statistics (ftk_spectrum_ex). Returns one result dict per job."""
+    import torch
+
+    from . import FTK_ENOCONV, Context
+    from ftk_inputs import named, omega_grid
+
+    sp0 = specs[0]
+    cl = sp0.cluster if sp0.cluster is not None else named(sp0.n_sites)
+    omega = omega_grid(*sp0.omega)
+    n_rhs = sum(sp.n_rhs for sp in specs)
+    block = 1
+    while block < n_rhs:
+        block <<= 1
+    stream = stream if stream is not None else torch.cuda.Stream()
+    ctx = Context(cl, sp0.K, sp0.J, sp0.precision, max_rhs=block, n_saved=max(sp.n_shells for sp in specs),
+                  stream=stream)
+    try:
+        slots, stats = [], []
+        for ji, sp in enumerate(specs):
+            ell = ell_for(cl, sp.K, sp.J, sp.ell)
+            ctx.tpq_init(sp.seed, sp.sample, ell)
+            u, lq, _ = ctx.tpq_step(sp.n_steps, sp.save_every)
+            steps, _ = ctx.shells()
+            stats.append((u, lq, ell, len(steps)))
+            for p, (g, qi) in enumerate(sp.probes):
+                for sh in range(len(steps)):
+                    ctx.apply_op(sh, g, cl.momenta[qi], len(slots))
+                    slots.append((ji, p, sh))
+        G, it, st = ctx.shifted_cocg(list(range(len(slots))), omega, sp0.eta, tol=sp0.tol, max_iter=sp0.max_iter,
+                                     allow_noconv=True)
+        out = []
+        for ji, sp in enumerate(specs):
+            u, lq, ell, n_sh = stats[ji]
+            Gj = {p: np.zeros((n_sh, len(omega)), dtype=np.complex128) for p in range(len(sp.probes))}
+            itj = {p: np.zeros(n_sh, dtype=np.int64) for p in range(len(sp.probes))}
+            noconv = False
+            for k, (jj, p, sh) in enumerate(slots):
+                if jj == ji:
+                    Gj[p][sh] = G[k]
+                    itj[p][sh] = it[k]
+                    noconv |= st == FTK_ENOCONV and it[k] >= sp.max_iter
+            spectra, trunc = {}, {}
+            temps = np.asarray(sp.temps, dtype=np.float64)
+            for p, probe in enumerate(sp.probes):
+                S, tr = ctx.spectrum_ex(Gj[p], temps, u, lq, sp.save_every, ell)
+                spectra[tuple(probe)] = S
+                trunc[tuple(probe)] = tr
+            out.append({"status": "noconv" if noconv else "ok", "spectra": spectra,
+                        "G": {tuple(sp.probes[p]): Gj[p] for p in Gj},
+                        "iters": {tuple(sp.probes[p]): itj[p] for p in itj}, "trunc": trunc, "packed": len(specs)})
+        return out
+    finally:
+        ctx.close()
+
+
 class Server:
     """Admission by footprint, up to max_slots concurrent jobs.
 
     runner(spec) -> dict (default: run_job on a new stream); footprint(spec)
     -> bytes (default: spec.footprint()); mem_budget: bytes (default: 90% of
-    the free device memory when the server starts).
+    the free device memory when the server starts). pack_rhs > 0: a job being
+    admitted takes waiting jobs with the same pack key along (in arrival
+    order, up to pack_rhs right-hand sides in all and while their summed
+    footprints fit), and the group runs as one blocked solve through
+    pack_runner(specs) -> [dict] (default: run_pack).
     """
 
     def __init__(self, max_slots=4, mem_budget=None, runner=None, footprint=None, max_skips=8,
-                 clock=time.perf_counter):
+                 clock=time.perf_counter, pack_rhs=0, pack_runner=None):
         self.max_slots = max_slots
         self.runner = runner or run_job
+        self.pack_rhs = int(pack_rhs)
+        self.pack_runner = pack_runner or run_pack
+        self.packs = []                   # job ids run together
         self.footprint = footprint or (lambda s: s.footprint())
         self.max_skips = max_skips
         self.clock = clock
@@ -255,9 +335,31 @@ class Server:
                 jid, spec, arrival, _ = self._pending[i]
                 del self._pending[i]
                 need = self.footprint(spec)
+                group = [(jid, spec, arrival)]
+                if self.pack_rhs > 0:
+                    # compatible waiting jobs join while the right-hand sides and memory allow
+                    rhs = spec.n_rhs
+                    free = self.mem_budget - self._mem_used - need
+                    key = spec.pack_key()
+                    k = 0
+                    while k < len(self._pending):
+                        j2, s2, a2, _ = self._pending[k]
+                        f2 = self.footprint(s2)
+                        if s2.pack_key() == key and rhs + s2.n_rhs <= self.pack_rhs and f2 <= free:
+                            group.append((j2, s2, a2))
+                            rhs += s2.n_rhs
+                            free -= f2
+                            need += f2
+                            del self._pending[k]
+                        else:
+                            k += 1
                 self._mem_used += need
                 self.peak_mem = max(self.peak_mem, self._mem_used)
-                th = threading.Thread(target=self._work, args=(jid, spec, arrival, need), daemon=True)
+                if len(group) == 1:
+                    th = threading.Thread(target=self._work, args=(jid, spec, arrival, need), daemon=True)
+                else:
+                    self.packs.append([g[0] for g in group])
+                    th = threading.Thread(target=self._work_pack, args=(group, need), daemon=True)
                 self._running[jid] = th
                 self.peak_running = max(self.peak_running, len(self._running))
                 self.admission_log.append((self.clock(), jid, self._mem_used))
@@ -271,6 +373,24 @@ class Server:
             if item[3] >= self.max_skips:
                 return None
         return None
+
+    def _work_pack(self, group, need):
+        start = self.clock()
+        try:
+            outs = self.pack_runner([g[1] for g in group])
+            res = [JobResult(j, o.get("status", "ok"), o.get("spectra", {}), o.get("G", {}), o.get("iters", {}),
+                             o.get("trunc", {})) for (j, _, _), o in zip(group, outs)]
+        except Exception as e:  # noqa: BLE001 - a failing pack must not stop the server
+            res = [JobResult(j, f"error: {type(e).__name__}: {e}") for j, _, _ in group]
+        fin = self.clock()
+        for r, (_, _, arrival) in zip(res, group):
+            r.arrival, r.start, r.finish = arrival, start, fin
+        with self._lock:
+            for r in res:
+                self._results[r.job_id] = r
+            self._mem_used -= need
+            del self._running[group[0][0]]
+            self._lock.notify_all()
 
     def _work(self, jid, spec, arrival, need):
         start = self.clock()

@@ -62,3 +62,40 @@ def test_alone_equals_mixed_and_matches_oracle():
         ref = dense.dense_estimator(dg, psi0, 0.5, sp.n_steps, sp.save_every, g, cl.momenta[qi], om, sp.eta,
                                     sp.temps)
         assert np.linalg.norm(S - ref["S"]) <= 1e-8 * np.linalg.norm(ref["S"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df"])
+def test_packed_jobs_equal_alone(prec):
+    """Three jobs on the same 12-site Hamiltonian (different seeds, probes and
+    temperatures) waiting together are packed into one blocked solve; each
+    job's spectra equal the job run alone (its own context and block) to 1e-9
+    (both solved to tol 1e-11; the block width changes the H.V plan, so the
+    rounding differs)."""
+    from paper_1802_02854_gb300 import build
+    build.build()
+    from paper_1802_02854_gb300 import serve
+
+    def job(seed, probes, temps):
+        return serve.JobSpec(n_sites=12, K=-1.0, J=0.1, seed=seed, n_steps=41, save_every=20, probes=probes,
+                             omega=(-2, 2, 96), eta=0.05, temps=temps, tol=1e-11, max_iter=5000, block=4,
+                             precision=prec)
+
+    specs = [job(21, [(2, 1)], [0.5, 1.0]), job(22, [(0, 2), (2, 3)], [0.7]), job(23, [(1, 4)], [0.4, 2.0])]
+    alone = []
+    for sp in specs:
+        srv = serve.Server(max_slots=1)
+        alone.append(srv.result(srv.submit(sp), timeout=600))
+        srv.close()
+    srv = serve.Server(max_slots=1, pack_rhs=32)
+    blocker = srv.submit(serve.JobSpec(n_sites=10, J=0.2, seed=1, n_steps=21, omega=(-2, 2, 64), eta=0.1,
+                                       tol=1e-8, temps=[1.0]))
+    ids = [srv.submit(sp) for sp in specs]
+    packed = [srv.result(j, timeout=600) for j in ids]
+    srv.result(blocker, timeout=600)
+    srv.close()
+    assert srv.packs and sorted(srv.packs[0]) == ids
+    for a, m in zip(alone, packed):
+        assert a.status == "ok" and m.status == "ok", (a.status, m.status)
+        for key in a.spectra:
+            assert np.linalg.norm(a.spectra[key] - m.spectra[key]) <= 1e-9 * np.linalg.norm(a.spectra[key])
+            assert a.trunc[key].tolist() == m.trunc[key].tolist()

@@ -120,3 +120,28 @@ def test_poisson_stream_is_seeded_and_in_range():
         assert 16 <= len(s.temps) <= 64 and s.omega[2] in (256, 512, 1024)
         assert all(0 <= g <= 2 and 0 <= q < s.n_sites // 2 for g, q in s.probes)
         assert s.precision in ("fp64", "df")
+
+
+def test_compatible_jobs_are_packed():
+    """pack_rhs: a job being admitted takes waiting jobs with the same pack key
+    (same Hamiltonian, precision, shifts, eta, tolerance) along, up to the
+    right-hand-side limit; other jobs run alone; every job gets its own result."""
+    calls = []
+
+    def pack_runner(specs):
+        calls.append([s.seed for s in specs])
+        time.sleep(0.02)
+        return [{"status": "ok", "spectra": {(2, 1): [[float(s.seed)]]}} for s in specs]
+
+    run = FakeRunner(delay=0.2)
+    srv = Server(max_slots=1, mem_budget=100_000, runner=run, footprint=fp, pack_rhs=8, pack_runner=pack_runner)
+    blocker = srv.submit(JobSpec(n_sites=8, J=0.3, seed=100))          # occupies the slot meanwhile
+    same = [srv.submit(JobSpec(n_sites=8, J=0.1, seed=s, probes=[(2, s % 4)], n_steps=41)) for s in range(5)]
+    other = srv.submit(JobSpec(n_sites=8, J=0.2, seed=50))              # another Hamiltonian
+    res = {j: srv.result(j, timeout=30) for j in [blocker, other] + same}
+    srv.close()
+    assert all(r.status == "ok" for r in res.values())
+    # 3 shells x 1 probe = 3 right-hand sides each: two jobs per pack of <= 8
+    assert calls == [[0, 1], [2, 3], [4]] or calls == [[0, 1], [2, 3]]
+    assert [res[j].spectra[(2, 1)][0][0] for j in same] == [0.0, 1.0, 2.0, 3.0, 4.0]
+    assert len(srv.packs) >= 2 and run.order[0] == 100 and 50 in run.order
