@@ -455,3 +455,31 @@ def test_hv_full_size_n28_fp32(ftk):
     del out
     ref = sparse.hv(cl, -1.0, 0.1, v.astype(np.complex128))
     assert rel(got, ref) <= TOL_HV["fp32"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df"])
+def test_truncated_solve_n24_vs_oracle(ftk, prec):
+    """Full size at 24 sites in the bench's labelling: a shifted solve of S^x_q
+    on a seeded state stopped after 6 iterations against the oracle's plain
+    two-term COCG stopped after 6 (the same sum of terms in exact
+    arithmetic): G at all 1024 shifts to 1e-10 of max |G| (the oracle's own
+    check at this size, where it cannot run a converged solve in seconds)."""
+    cl = _bench_cluster_n24(ftk)
+    K, J = -1.0, 0.05
+    psi0 = random_state(24, 240)
+    q = cl.momenta[1]
+    ctx = ftk.Context(cl, K, J, prec, max_rhs=1, n_saved=1)
+    ctx.set_state(psi0, 0.5)
+    ctx.tpq_step(1, 1)
+    steps, en = ctx.shells()
+    ctx.apply_op(0, 0, q, 0)
+    omega = omega_grid(-3, 3, 1024)
+    eta = 0.01
+    G, it, st = ctx.shifted_cocg([0], omega, eta, tol=1e-14, max_iter=6, allow_noconv=True)
+    ctx.close()
+    assert it[0] == 6 and st == ftk.FTK_ENOCONV
+    lam = sparse.apply_op(cl, 0, q, psi0)
+    z = en[0] + omega + 1j * eta
+    Gr, itr, _, str_ = sparse.cocg(cl, K, J, lam, z[512], z, 1e-14, 6)
+    assert itr == 6 and str_ == 1
+    assert np.abs(G[0] - Gr).max() <= 1e-10 * np.abs(Gr).max()

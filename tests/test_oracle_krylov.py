@@ -106,6 +106,25 @@ def test_philox_known_answers():
         assert sparse.philox4x32_10(ctr, key).tolist() == want
 
 
+def test_gaussian_state_element_from_the_known_answer():
+    """Element 0 of seed 0, sample 0 draws Philox4x32-10 at counter (0, 0, 0, 0)
+    and key (0, 0): the first published known-answer vector. Its words give
+    u1 = ((w0 << 32 | w1) >> 11 + 1/2) 2^-53 and u2 from (w2, w3), and the
+    element is sqrt(-2 ln u1) exp(2 pi i u2) before normalisation: its phase
+    is 2 pi u2 whatever the norm. Swapped halves (u1 for u2), a swapped word
+    order or a sign slip in the angle all change it."""
+    ctr, key, want = _kat()[0]
+    assert ctr == [0, 0, 0, 0] and key == [0, 0]
+    u1 = ((((want[0] << 32) | want[1]) >> 11) + 0.5) * 2.0 ** -53
+    u2 = ((((want[2] << 32) | want[3]) >> 11) + 0.5) * 2.0 ** -53
+    for n in (4, 10):
+        v = sparse.gaussian_state(n, 0, 0)
+        ph = np.angle(v[0]) % (2 * np.pi)
+        assert abs(ph - 2 * np.pi * u2) <= 1e-12
+    # the angle of the other half (u1) would differ by far more than the bar
+    assert 0.0 < u1 < 1.0 and abs(2 * np.pi * u1 - 2 * np.pi * u2) > 0.1
+
+
 def test_gaussian_state_properties():
     """Normalised; real and imaginary parts i.i.d. with equal variance;
     seed and sample select independent streams."""
