@@ -26,7 +26,8 @@ single-vector FTKomega on the same GPU (same input), both spectra's error
 against a converged FP64 reference (tol 1e-9), per-step latency p50/p99, a
 serving stream's p50/p99, the roofline of the dominant kernel (the
 double-float H.V of the solve, timed alone, against the HBM copy rate, with
-its FP32-pipe fraction beside it) and the FP32 and FP64 H.V.
+its FP32-pipe fraction beside it), the FP32 H.V at 24, 26, 28 and 30 sites
+and the FP64 H.V.
 
 --impl reference runs the oracle (plain C/OpenMP FP64, test infrastructure)
 on the host cores on a bounded sample of the same workload.
@@ -391,6 +392,23 @@ def run_gpu(args):
                           "frac": round(2 * dim * 8 / t_hv1 / 1e9 / peak, 4), "peak": peak,
                           "peak_kind": peak_kind, "passes": p1[0]}
 
+    # the metric's H.v over the cluster sizes of the workloads (24-30 sites):
+    # FP32, one vector, sites relabelled for FP32 tiles, all passes
+    by_n = {}
+    if not args.no_n_sweep:
+        for n in (26, 28, 30):
+            cn = named(n)
+            perm_n, _ = ftk.ftk_suggest_order(n, cn.bonds, ftk.FTK_FP32, 1)
+            cn = relabel(cn, perm_n)
+            cx = ftk.Context(cn, K_COUPLING, J_COUPLING, "fp32", max_rhs=1)
+            t_n = time_hv(cx, torch, 1, torch.complex64, reps=4)
+            gbs_n = 2 * (1 << n) * 8 / t_n / 1e9
+            by_n[str(n)] = {"us": round(t_n * 1e6, 1), "gbs": round(gbs_n, 1), "frac": round(gbs_n / peak, 4),
+                            "passes": cx.plan_info()[0], "tile_bits": cx.plan_info()[1]}
+            cx.close()
+            torch.cuda.empty_cache()
+    roof["hv_fp32_by_n"] = by_n
+
     # the batched configuration's knob: FP64 blocked H.V time per column
     # against the block width (tile size and column chunk autotuned per width)
     blocked = {"B": [], "us_per_column": [], "plan": []}
@@ -537,6 +555,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-block-sweep", action="store_true", help="skip the FP64 block-width sweep")
+    ap.add_argument("--no-n-sweep", action="store_true", help="skip the FP32 H.v at 26, 28 and 30 sites")
     ap.add_argument("--hv-only", action="store_true", help="only a few H.V launches (profiling)")
     ap.add_argument("--hv-sites", type=int, default=N_SITES)
     ap.add_argument("--hv-prec", default="fp32", choices=["fp64", "fp32", "df"])

@@ -3,4 +3,4 @@
 Holds geometry and random inputs only, none of the method's arithmetic.
 """
 from .lattice import Cluster, honeycomb, named, relabel, translations, characters, GAMMA_X, GAMMA_Y, GAMMA_Z  # noqa: F401
-from .states import random_state, random_vectors, omega_grid, log_temperatures  # noqa: F401
+from .states import random_state, random_vectors, hashed_amplitudes, omega_grid, log_temperatures  # noqa: F401

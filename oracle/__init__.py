@@ -23,6 +23,8 @@ Parts:
   sector.py   momentum sectors of the translation group: the sector basis
               from its definition, the sector block of H, projection and
               embedding.
+  rows.py     sampled rows of H v from the spin matrix elements, for
+              clusters (26, 30 sites) where no full product fits a test.
 
 Every function is pinned by -m "not gpu" tests (tests/test_oracle_*.py)
 against closed forms, brute force, invariants and published test vectors.

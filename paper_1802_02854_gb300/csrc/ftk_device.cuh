@@ -28,39 +28,45 @@ template <> struct Acc<double> {
     __device__ __forceinline__ void fma2(double a, double b) { s = fma(a, b, s); }
     __device__ __forceinline__ double get() const { return s; }
 };
+// The error-free steps are written with the rounded intrinsics (__fadd_rn,
+// __fmul_rn, which the compiler never contracts into an FMA): a contracted
+// t = s + a b would no longer be the rounded sum the two-sum corrects.
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 template <> struct Acc<float> {
     float s, c;
     __device__ Acc() : s(0.f), c(0.f) {}
     __device__ __forceinline__ void add(float v) {
-        float t = s + v;
-        float bp = t - s;
-        float err = (s - (t - bp)) + (v - bp);
+        const float t = fadd(s, v);
+        const float bp = fsub(t, s);
+        const float err = fadd(fsub(s, fsub(t, bp)), fsub(v, bp));
         s = t;
-        c += err;
+        c = fadd(c, err);
     }
     __device__ __forceinline__ void fma2(float a, float b) {
-        float p = a * b;
-        float e = fmaf(a, b, -p);
+        const float p = fmul(a, b);
+        const float e = fmaf(a, b, -p);
         add(p);
-        c += e;
+        c = fadd(c, e);
     }
     // adds (ah + al)(bh + bl): the hi x hi product exactly (FMA two-product),
     // the cross terms in float (their lo x lo term is below the pair precision)
     __device__ __forceinline__ void fma_pair(float ah, float al, float bh, float bl) {
-        float p = ah * bh;
+        const float p = fmul(ah, bh);
         float e = fmaf(ah, bh, -p);
         e = fmaf(ah, bl, e);
         e = fmaf(al, bh, e);
         add(p);
-        c += e;
+        c = fadd(c, e);
     }
     // adds (ah + al) b
     __device__ __forceinline__ void fma_hl(float ah, float al, float b) {
-        float p = ah * b;
+        const float p = fmul(ah, b);
         float e = fmaf(ah, b, -p);
         e = fmaf(al, b, e);
         add(p);
-        c += e;
+        c = fadd(c, e);
     }
     __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
@@ -145,37 +151,38 @@ namespace ftk {
 
 struct dfl { float hi, lo; };
 
-__host__ __device__ __forceinline__ dfl dfl_two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
+// Device only, with the rounded intrinsics of Acc<float> (no contraction).
+__device__ __forceinline__ dfl dfl_two_sum(float a, float b) {
+    const float s = fadd(a, b);
+    const float bb = fsub(s, a);
+    return {s, fadd(fsub(a, fsub(s, bb)), fsub(b, bb))};
 }
-__host__ __device__ __forceinline__ dfl dfl_fast(float a, float b) {   // |a| >= |b| or a == 0
-    const float s = a + b;
-    return {s, b - (s - a)};
+__device__ __forceinline__ dfl dfl_fast(float a, float b) {   // |a| >= |b| or a == 0
+    const float s = fadd(a, b);
+    return {s, fsub(b, fsub(s, a))};
 }
-__host__ __device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
     const dfl s = dfl_two_sum(a.hi, b.hi);
-    return dfl_fast(s.hi, s.lo + (a.lo + b.lo));
+    return dfl_fast(s.hi, fadd(s.lo, fadd(a.lo, b.lo)));
 }
-__host__ __device__ __forceinline__ dfl dfl_neg(dfl a) { return {-a.hi, -a.lo}; }
-__host__ __device__ __forceinline__ dfl dfl_sub(dfl a, dfl b) { return dfl_add(a, dfl_neg(b)); }
-__host__ __device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
-    const float p = a.hi * b.hi;
+__device__ __forceinline__ dfl dfl_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl dfl_sub(dfl a, dfl b) { return dfl_add(a, dfl_neg(b)); }
+__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
+    const float p = fmul(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
     return dfl_fast(p, e);
 }
-__host__ __device__ __forceinline__ dfl dfl_from(double d) {
+__device__ __forceinline__ dfl dfl_from(double d) {
     const float h = (float)d;
     return {h, (float)(d - (double)h)};
 }
 
 struct dcl { dfl re, im; };
-__host__ __device__ __forceinline__ dcl dcl_add(dcl a, dcl b) { return {dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
-__host__ __device__ __forceinline__ dcl dcl_sub(dcl a, dcl b) { return {dfl_sub(a.re, b.re), dfl_sub(a.im, b.im)}; }
-__host__ __device__ __forceinline__ dcl dcl_mul(dcl a, dcl b) {
+__device__ __forceinline__ dcl dcl_add(dcl a, dcl b) { return {dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
+__device__ __forceinline__ dcl dcl_sub(dcl a, dcl b) { return {dfl_sub(a.re, b.re), dfl_sub(a.im, b.im)}; }
+__device__ __forceinline__ dcl dcl_mul(dcl a, dcl b) {
     return {dfl_sub(dfl_mul(a.re, b.re), dfl_mul(a.im, b.im)), dfl_add(dfl_mul(a.re, b.im), dfl_mul(a.im, b.re))};
 }
 
@@ -195,13 +202,13 @@ __device__ __forceinline__ DfStep df_step(const CocgSeed &s) {
 // plus the cross terms, added by a two-sum whose error goes to acc.lo (the
 // lo x lo term is below the pair precision). 12 FP32 operations.
 __device__ __forceinline__ void dfl_mac(dfl &acc, dfl a, dfl b) {
-    const float p = a.hi * b.hi;
+    const float p = fmul(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
-    const float t = acc.hi + p;
-    const float bb = t - acc.hi;
-    acc.lo += ((acc.hi - (t - bb)) + (p - bb)) + e;
+    const float t = fadd(acc.hi, p);
+    const float bb = fsub(t, acc.hi);
+    acc.lo = fadd(acc.lo, fadd(fadd(fsub(acc.hi, fsub(t, bb)), fsub(p, bb)), e));
     acc.hi = t;
 }
 // Renormalised pair of an accumulator (two-sum: no ordering assumption).
@@ -232,7 +239,7 @@ __device__ __forceinline__ dcl df_next_residual(const dcl &rc, const dcl &rp, co
     dfl_mac(ni, dfl_neg(q.al.im), ar);
     nr = dfl_renorm(nr);
     ni = dfl_renorm(ni);
-    if (q.f != 1.f) { nr = {nr.hi * q.f, nr.lo * q.f}; ni = {ni.hi * q.f, ni.lo * q.f}; }
+    if (q.f != 1.f) { nr = {fmul(nr.hi, q.f), fmul(nr.lo, q.f)}; ni = {fmul(ni.hi, q.f), fmul(ni.lo, q.f)}; }
     return {nr, ni};
 }
 // Per-thread sums of rho = r^T r, g = lambda^dag r (double-float: exact

@@ -483,3 +483,64 @@ def test_truncated_solve_n24_vs_oracle(ftk, prec):
     Gr, itr, _, str_ = sparse.cocg(cl, K, J, lam, z[512], z, 1e-14, 6)
     assert itr == 6 and str_ == 1
     assert np.abs(G[0] - Gr).max() <= 1e-10 * np.abs(Gr).max()
+
+
+def _hashed_on_device(torch, n, seed, split):
+    """The vector of ftk_inputs.hashed_amplitudes built on the device in
+    slices: complex64 [dim] (FP32), or [2, dim] hi and lo parts (split)."""
+    from ftk_inputs import hashed_amplitudes
+    dim = 1 << n
+    v = torch.empty((2, dim) if split else (dim,), dtype=torch.complex64, device="cuda")
+    step = 1 << 24
+    for s0 in range(0, dim, step):
+        idx = torch.arange(s0, min(dim, s0 + step), dtype=torch.int64, device="cuda")
+        a = hashed_amplitudes(idx, seed, xp=torch)          # float64 (re, im)
+        hi = a.float()
+        if split:
+            v[0, s0:s0 + idx.numel()] = torch.view_as_complex(hi.contiguous())
+            v[1, s0:s0 + idx.numel()] = torch.view_as_complex((a - hi.double()).float().contiguous())
+        else:
+            v[s0:s0 + idx.numel()] = torch.view_as_complex(hi.contiguous())
+        del idx, a, hi
+    return v
+
+
+@pytest.mark.parametrize("n,prec", [(26, "fp32"), (26, "df"), (30, "fp32"), (30, "df")])
+def test_hv_sampled_rows_large_clusters(ftk, n, prec):
+    """26 and 30 sites (2^30 amplitudes: 8 GB FP32, 16 GB double-float per
+    vector), sites relabelled as the bench does: the product's H v on 4096
+    sampled rows (and the first and last) against the oracle's rows from the
+    spin matrix elements, with the input evaluated element by element from
+    the same counter-based generator. Bars: 1e-6 (FP32) and 1e-12
+    (double-float) relative over the sample."""
+    import torch
+    from ftk_inputs import hashed_amplitudes
+    from oracle import rows
+    K, J, seed = -1.0, 0.05, 2024 + n
+    cl0 = named(n)
+    perm, _ = ftk.ftk_suggest_order(n, cl0.bonds, ftk.PRECISIONS[prec], 1)
+    cl = relabel(cl0, perm)
+    xs = np.concatenate([[0, (1 << n) - 1], np.random.default_rng(n).integers(0, 1 << n, 4096)]).astype(np.int64)
+    v = _hashed_on_device(torch, n, seed, prec == "df")
+    # the device input is the generator's vector, element for element
+    vi = torch.from_numpy(xs).cuda()
+    want = hashed_amplitudes(xs, seed)
+    if prec == "df":
+        got_in = v[0, vi].cpu().numpy().astype(np.complex128) + v[1, vi].cpu().numpy().astype(np.complex128)
+        assert np.abs(got_in - want).max() <= 1e-14
+    else:
+        assert np.array_equal(v[vi].cpu().numpy(), want.astype(np.complex64))
+    ctx = ftk.Context(cl, K, J, prec, max_rhs=1)
+    out = ctx.hv(v)
+    torch.cuda.synchronize()
+    if prec == "df":
+        got = out[0, vi].cpu().numpy().astype(np.complex128) + out[1, vi].cpu().numpy().astype(np.complex128)
+    else:
+        got = out[vi].cpu().numpy().astype(np.complex128)
+    n_pass = ctx.plan_info()[0]
+    ctx.close()
+    del v, out
+    torch.cuda.empty_cache()
+    ref = rows.hv_rows(cl, K, J, lambda idx: hashed_amplitudes(idx, seed), xs)
+    assert n_pass >= 3
+    assert rel(got, ref) <= (1e-12 if prec == "df" else 1e-6)

@@ -161,3 +161,30 @@ def test_ell_lower_bound_keeps_l_minus_h_positive():
         lmin = cl.n_bonds * ev[-1] / cl.n_sites
         e = np.linalg.eigvalsh(dense.hamiltonian(cl, K, J))
         assert lmin - e.max() / cl.n_sites >= -1e-12
+
+
+@pytest.mark.parametrize("n", [2, 8, 12])
+@pytest.mark.parametrize("K,J", KJ)
+def test_sampled_rows_equal_kronecker(n, K, J):
+    """Brute force: the row-by-row product of oracle/rows.py (spin matrix
+    elements per bond) == the Kronecker-product H v, on every row."""
+    from oracle import rows
+    cl = named(n)
+    h = dense.hamiltonian_sparse(cl, K, J)
+    v = random_state(n, 11)
+    xs = np.arange(1 << n, dtype=np.int64)
+    got = rows.hv_rows(cl, K, J, lambda idx: v[idx], xs)
+    ref = h @ v
+    assert np.linalg.norm(got - ref) <= 1e-14 * np.linalg.norm(ref)
+
+
+def test_sampled_rows_of_a_bigger_cluster():
+    """At N = 16 on random rows: the row formula against the matrix-free C
+    product (two independent codings of the same matrix elements)."""
+    from oracle import rows
+    cl = named(16)
+    v = random_state(16, 5)
+    xs = np.random.default_rng(3).integers(0, 1 << 16, 512)
+    got = rows.hv_rows(cl, -1.0, 0.05, lambda idx: v[idx], xs)
+    ref = sparse.hv(cl, -1.0, 0.05, v)[xs]
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
