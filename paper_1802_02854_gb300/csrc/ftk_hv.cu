@@ -116,24 +116,42 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
     // element offset of (offset t + T k, column j) from the tile base:
     // st + ksp(k) + j ld, with st / ksp the global bits of the thread /
     // register part (disjoint bits, so OR = sum)
-    uint64_t st = 0;
+    // (32-bit: a column has at most 2^FTK_MAX_SITES elements)
+    uint32_t st = 0;
     for (int q = 0; q < tb; ++q)
-        if ((t >> q) & 1) st |= 1ull << pd.tile_pos[q];
-    long long kofs[LE > 0 ? LE : 1];
+        if ((t >> q) & 1) st |= 1u << pd.tile_pos[q];
+    uint32_t kofs[LE > 0 ? LE : 1];
 #pragma unroll
-    for (int q = 0; q < LE; ++q) kofs[q] = (long long)(1ull << pd.tile_pos[tb + q]);
-    auto eofs = [&](int k) -> long long {
-        long long v = (long long)st;
+    for (int q = 0; q < LE; ++q) kofs[q] = 1u << pd.tile_pos[tb + q];
+    auto eofs = [&](int k) -> uint32_t {
+        uint32_t v = st;
 #pragma unroll
         for (int q = 0; q < LE; ++q)
             if ((k >> q) & 1) v += kofs[q];
         return v;
     };
+    // tile offsets: the bits of the tile index deposited at the free sites.
+    // Successive tiles of a CTA are gridDim.x apart; their offsets follow by
+    // a masked addition (the bits outside the mask set to 1 carry across
+    // them): dep(a + g) = ((dep(a) | ~mask) + dep(g)) & mask.
     auto tile_ofs = [&](long tau) -> long long {
         uint64_t v = 0;
         for (int q = 0; q < pd.n_free; ++q)
             if ((tau >> q) & 1) v |= 1ull << pd.free_pos[q];
         return (long long)v;
+    };
+    // (mask and step in shared memory: read once per tile, no registers held)
+    __shared__ uint64_t free_mask, dep_grid;
+    if (threadIdx.x == 0) {
+        uint64_t m = 0;
+        for (int q = 0; q < pd.n_free; ++q) m |= 1ull << pd.free_pos[q];
+        free_mask = m;
+        dep_grid = (uint64_t)tile_ofs(gridDim.x);
+    }
+    __syncthreads();
+    auto next_ofs = [&](long long ofs) -> long long {
+        const uint64_t m = free_mask;
+        return (long long)((((uint64_t)ofs | ~m) + dep_grid) & m);
     };
     // diagonal of this pass's bonds at the thread's offsets: dgv[0] c0 +
     // dgv[1] c1 with integer counts c (+1 parallel, -1 antiparallel; parity
@@ -199,7 +217,7 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
         cx *nxt = (it & 1) ? buf0 : buf1;
         const long tn = tau + gridDim.x;
         const bool more = tn < n_tiles;
-        const long long tofs_n = more ? tile_ofs(tn) : 0;
+        const long long tofs_n = more ? next_ofs(tofs) : 0;
         if (more) issue(in, tofs_n, nxt);
         // v of this tile: everything but the newest one (first pass) or two groups
         if (first) { if (more) cp_async_wait<1>(); else cp_async_wait<0>(); }
@@ -444,11 +462,28 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
             if ((k >> q) & 1) v += kofs[q];
         return v;
     };
+    // tile offsets: the bits of the tile index deposited at the free sites.
+    // Successive tiles of a CTA are gridDim.x apart; their offsets follow by
+    // a masked addition (the bits outside the mask set to 1 carry across
+    // them): dep(a + g) = ((dep(a) | ~mask) + dep(g)) & mask.
     auto tile_ofs = [&](long tau) -> long long {
         uint64_t v = 0;
         for (int q = 0; q < pd.n_free; ++q)
             if ((tau >> q) & 1) v |= 1ull << pd.free_pos[q];
         return (long long)v;
+    };
+    // (mask and step in shared memory: read once per tile, no registers held)
+    __shared__ uint64_t free_mask, dep_grid;
+    if (threadIdx.x == 0) {
+        uint64_t m = 0;
+        for (int q = 0; q < pd.n_free; ++q) m |= 1ull << pd.free_pos[q];
+        free_mask = m;
+        dep_grid = (uint64_t)tile_ofs(gridDim.x);
+    }
+    __syncthreads();
+    auto next_ofs = [&](long long ofs) -> long long {
+        const uint64_t m = free_mask;
+        return (long long)((((uint64_t)ofs | ~m) + dep_grid) & m);
     };
     // diagonal dgv[0] c0 + dgv[1] c1 (integer counts c as in the kernel
     // above) in double-float arithmetic, once per thread
@@ -483,13 +518,13 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
     DfUpdDots udots;
     auto issue = [&](const float2 *src, long long tofs, float4 *b) {
         if (act) {
-            const float2 *g = src + tofs;
+            const float2 *g = src + tofs, *gl = g + lo;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                const float2 *gk = g + eofs(k);
+                const long long e = eofs(k);
                 float2 *d = reinterpret_cast<float2 *>(b + t + T * k);
-                cp_async_elem(d, gk);
-                cp_async_elem(d + 1, gk + lo);
+                cp_async_elem(d, g + e);
+                cp_async_elem(d + 1, gl + e);
             }
         }
         cp_async_commit();
@@ -506,7 +541,7 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
         float4 *nb = (it & 1) ? b0 : b1;
         const long tn = tau + gridDim.x;
         const bool more = tn < n_tiles;
-        const long long tofs_n = more ? tile_ofs(tn) : 0;
+        const long long tofs_n = more ? next_ofs(tofs) : 0;
         if (!FU && more) issue(in, tofs_n, nb);
         if (first) { if (more) cp_async_wait<1>(); else cp_async_wait<0>(); }
         else { if (more) cp_async_wait<2>(); else cp_async_wait<1>(); }
@@ -622,15 +657,15 @@ hv_pass_df_kernel(const float2 *__restrict__ in, float2 *out, const PassDesc pd,
                     df_add_to2(ah[k], al[k], make_float2(v4.x, v4.y), make_float2(v4.z, v4.w));
                 }
             }
-            float2 *o = out + tofs;
+            float2 *o = out + tofs, *ol = o + lo;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 // renormalise (fast two-sum) and store hi, lo
                 const float2 hh = __fadd2_rn(ah[k], al[k]);
                 const float2 ll = fsub2(al[k], fsub2(hh, ah[k]));
-                float2 *ok = o + eofs(k);
-                ok[0] = hh;
-                ok[lo] = ll;
+                const long long e = eofs(k);
+                o[e] = hh;
+                ol[e] = ll;
                 if (EPI == EPI_COCG && pd.last) {
                     // mu = r^T w (bilinear) in double-float from hi + lo
                     dot[0].fma_pair(ph[k].x, pl[k].x, hh.x, ll.x);
