@@ -93,7 +93,11 @@ __device__ __forceinline__ void bond_apply(typename C2<R>::t (&acc)[1 << LE][B],
         if constexpr (KA < LE && KB < LE) bond_apply<R, B, LE, KA, KB>(acc, pv, cs, cf);    \
         break;
 
-template <typename R, int B, int LE, int EPI>
+// TB > 0: the thread bits of the tile (tile_bits - LE) as a compile-time
+// constant, so that the strides T k of the shared tile fold into immediate
+// offsets (one vector with 512 threads: the 2^13-amplitude FP32 and
+// 2^12-amplitude FP64 tiles, TB = 9).
+template <typename R, int B, int LE, int EPI, int TB = 0>
 __global__ void __launch_bounds__(512, 1)
 hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out, long long ld, const PassDesc pd,
                const EpiArgs ea) {
@@ -102,7 +106,7 @@ hv_pass_kernel(const typename C2<R>::t *__restrict__ in, typename C2<R>::t *out,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (ea.all_done && *ea.all_done) return;
     if (ea.lowp && *ea.lowp != ea.lowp_run) return;
-    const int b = pd.tile_bits;
+    const int b = TB > 0 ? TB + LE : pd.tile_bits;
     const int tb = b - LE;
     const int tile_n = 1 << b;
     const int T = 1 << tb;
@@ -850,16 +854,23 @@ static cudaError_t opt_in(K kern) {
     return e;
 }
 
+template <typename R, int B, int LE, int TB>
+static cudaError_t attrs_le_tb() {
+    cudaError_t e = opt_in(hv_pass_kernel<R, B, LE, EPI_PLAIN, TB>);
+    if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, B, LE, EPI_COCG, TB>);
+    if constexpr (sizeof(R) == 4)
+        if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, B, LE, EPI_COCG_MIXED, TB>);
+    if constexpr (B == 1)
+        if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, 1, LE, EPI_TPQ, TB>);
+    if constexpr (B == 1 && sizeof(R) == 8)
+        if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, 1, LE, EPI_TAYLOR, TB>);
+    return e;
+}
 template <typename R, int B, int LE>
 static cudaError_t attrs_le() {
-    cudaError_t e = opt_in(hv_pass_kernel<R, B, LE, EPI_PLAIN>);
-    if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, B, LE, EPI_COCG>);
-    if constexpr (sizeof(R) == 4)
-        if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, B, LE, EPI_COCG_MIXED>);
-    if constexpr (B == 1)
-        if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, 1, LE, EPI_TPQ>);
-    if constexpr (B == 1 && sizeof(R) == 8)
-        if (e == cudaSuccess) e = opt_in(hv_pass_kernel<R, 1, LE, EPI_TAYLOR>);
+    cudaError_t e = attrs_le_tb<R, B, LE, 0>();
+    if constexpr (B == 1 && LE > 0)
+        if (e == cudaSuccess) e = attrs_le_tb<R, 1, LE, 9>();
     return e;
 }
 
@@ -905,21 +916,28 @@ cudaError_t init_kernel_attributes() {
     return status;
 }
 
+template <typename R, int B, int LE, int TB>
+static void (*pass_kernel(int epi))(const typename C2<R>::t *, typename C2<R>::t *, long long, const PassDesc,
+                                    const EpiArgs) {
+    if (epi == EPI_PLAIN) return hv_pass_kernel<R, B, LE, EPI_PLAIN, TB>;
+    if (epi == EPI_COCG) return hv_pass_kernel<R, B, LE, EPI_COCG, TB>;
+    if constexpr (sizeof(R) == 4)
+        if (epi == EPI_COCG_MIXED) return hv_pass_kernel<R, B, LE, EPI_COCG_MIXED, TB>;
+    if constexpr (B == 1) {
+        if (epi == EPI_TPQ) return hv_pass_kernel<R, 1, LE, EPI_TPQ, TB>;
+        if constexpr (sizeof(R) == 8)
+            if (epi == EPI_TAYLOR) return hv_pass_kernel<R, 1, LE, EPI_TAYLOR, TB>;
+    }
+    return nullptr;
+}
+
 template <typename R, int B, int LE>
 static cudaError_t launch_le(int epi, const void *in, void *out, long long ld, const PassDesc &pd, const EpiArgs &ea,
                              int grid_cap, cudaStream_t st) {
     typedef typename C2<R>::t cx;
-    void (*k)(const cx *, cx *, long long, const PassDesc, const EpiArgs) = nullptr;
-    if (epi == EPI_PLAIN) k = hv_pass_kernel<R, B, LE, EPI_PLAIN>;
-    else if (epi == EPI_COCG) k = hv_pass_kernel<R, B, LE, EPI_COCG>;
-    else if constexpr (sizeof(R) == 4) {
-        if (epi == EPI_COCG_MIXED) k = hv_pass_kernel<R, B, LE, EPI_COCG_MIXED>;
-    }
-    else if constexpr (B == 1) {
-        if (epi == EPI_TPQ) k = hv_pass_kernel<R, 1, LE, EPI_TPQ>;
-        if constexpr (sizeof(R) == 8)
-            if (epi == EPI_TAYLOR) k = hv_pass_kernel<R, 1, LE, EPI_TAYLOR>;
-    }
+    void (*k)(const cx *, cx *, long long, const PassDesc, const EpiArgs) = pass_kernel<R, B, LE, 0>(epi);
+    if constexpr (B == 1 && LE > 0)
+        if (pd.tile_bits == 9 + LE) k = pass_kernel<R, 1, LE, 9>(epi);
     if (!k) return cudaErrorInvalidValue;
     const int threads = hv_threads(pd);
     const size_t smem = hv_smem_bytes(sizeof(R) == 8 ? 0 : 1, pd.cols, pd);
