@@ -87,6 +87,7 @@ struct CocgSeed {
     double alpha_prev_re, alpha_prev_im;
     double beta_prev_re, beta_prev_im;  // beta_{k-1}
     double c_re, c_im;          // c_k = beta_{k-1} alpha_k / alpha_{k-1}
+    double a1_re, a1_im;        // 1 + c_k - alpha_k z_s: coefficient of r_k in r_{k+1}
     double g_re, g_im;          // g_k = lambda^dagger r_k
     double nrm;                 // ||r_k||
     double resid;               // last max_s ||r_k|| / |pi^s_k| / ||lambda||

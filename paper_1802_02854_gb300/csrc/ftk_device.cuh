@@ -188,14 +188,14 @@ __device__ __forceinline__ dcl dcl_mul(dcl a, dcl b) {
 
 // ------------------------------------------------ COCG residual, split form
 // The scalars of one COCG step for one right-hand side as double-float
-// pairs: seed shift z_s, alpha_k, c_k, and the range-guard factor f (a power
-// of two, 1 when unused).
+// pairs: a1 = 1 + c_k - alpha_k z_s (formed in FP64 by the seed kernel),
+// alpha_k, c_k, and the range-guard factor f (a power of two, 1 when unused).
 struct DfStep {
-    dcl zs, al, cc;
+    dcl a1, al, cc;
     float f;
 };
 __device__ __forceinline__ DfStep df_step(const CocgSeed &s) {
-    return {{dfl_from(s.zs_re), dfl_from(s.zs_im)}, {dfl_from(s.alpha_re), dfl_from(s.alpha_im)},
+    return {{dfl_from(s.a1_re), dfl_from(s.a1_im)}, {dfl_from(s.alpha_re), dfl_from(s.alpha_im)},
             {dfl_from(s.c_re), dfl_from(s.c_im)}, (float)s.rescale};
 }
 // acc += a b in double-float: the hi x hi product exactly (FMA two-product)
@@ -214,29 +214,27 @@ __device__ __forceinline__ void dfl_mac(dfl &acc, dfl a, dfl b) {
 // Renormalised pair of an accumulator (two-sum: no ordering assumption).
 __device__ __forceinline__ dfl dfl_renorm(dfl a) { return dfl_two_sum(a.hi, a.lo); }
 
-// Three-term COCG residual (Sec. IV): A r_k = z_s r_k - w_k with w_k = H r_k,
-// r_{k+1} = r_k + c_k (r_k - r_{k-1}) - alpha_k A r_k, scaled by f. The
-// intermediate quantities are those of the formula (A r_k and r_k - r_{k-1}
-// are formed first); each real component accumulates its products with
-// dfl_mac and is renormalised once.
+// Three-term COCG residual (Sec. IV): with w_k = H r_k,
+// r_{k+1} = r_k + c_k (r_k - r_{k-1}) - alpha_k (z_s r_k - w_k)
+//         = a1 r_k - c_k r_{k-1} + alpha_k w_k,   a1 = 1 + c_k - alpha_k z_s,
+// scaled by f. Each real component is the double-float sum of six products
+// (the first one exact, then multiply-accumulates), renormalised once; its
+// rounding error is bounded by 2^-48 (|a1| |r_k| + |c_k| |r_{k-1}| +
+// |alpha_k| |w_k|), no more than that of forming z_s r_k - w_k and
+// r_k - r_{k-1} first.
 __device__ __forceinline__ dcl df_next_residual(const dcl &rc, const dcl &rp, const dcl &w, const DfStep &q) {
-    dfl ar = dfl_neg(w.re), ai = dfl_neg(w.im);
-    dfl_mac(ar, q.zs.re, rc.re);
-    dfl_mac(ar, dfl_neg(q.zs.im), rc.im);
-    dfl_mac(ai, q.zs.re, rc.im);
-    dfl_mac(ai, q.zs.im, rc.re);
-    ar = dfl_renorm(ar);
-    ai = dfl_renorm(ai);
-    const dfl dr = dfl_sub(rc.re, rp.re), di = dfl_sub(rc.im, rp.im);
-    dfl nr = rc.re, ni = rc.im;
-    dfl_mac(nr, q.cc.re, dr);
-    dfl_mac(nr, dfl_neg(q.cc.im), di);
-    dfl_mac(nr, dfl_neg(q.al.re), ar);
-    dfl_mac(nr, q.al.im, ai);
-    dfl_mac(ni, q.cc.re, di);
-    dfl_mac(ni, q.cc.im, dr);
-    dfl_mac(ni, dfl_neg(q.al.re), ai);
-    dfl_mac(ni, dfl_neg(q.al.im), ar);
+    dfl nr = dfl_mul(q.a1.re, rc.re);
+    dfl_mac(nr, dfl_neg(q.a1.im), rc.im);
+    dfl_mac(nr, dfl_neg(q.cc.re), rp.re);
+    dfl_mac(nr, q.cc.im, rp.im);
+    dfl_mac(nr, q.al.re, w.re);
+    dfl_mac(nr, dfl_neg(q.al.im), w.im);
+    dfl ni = dfl_mul(q.a1.re, rc.im);
+    dfl_mac(ni, q.a1.im, rc.re);
+    dfl_mac(ni, dfl_neg(q.cc.re), rp.im);
+    dfl_mac(ni, dfl_neg(q.cc.im), rp.re);
+    dfl_mac(ni, q.al.re, w.im);
+    dfl_mac(ni, q.al.im, w.re);
     nr = dfl_renorm(nr);
     ni = dfl_renorm(ni);
     if (q.f != 1.f) { nr = {fmul(nr.hi, q.f), fmul(nr.lo, q.f)}; ni = {fmul(ni.hi, q.f), fmul(ni.lo, q.f)}; }

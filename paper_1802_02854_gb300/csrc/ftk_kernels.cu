@@ -359,6 +359,8 @@ __device__ void seed_one(const SeedArgs &sa, CocgSeed &s, int j) {
     s.alpha_re = alpha.re; s.alpha_im = alpha.im;
     s.beta_prev_re = beta.re; s.beta_prev_im = beta.im;
     s.c_re = c.re; s.c_im = c.im;
+    const dcx az = cmul(alpha, zs);   // r_{k+1} = a1 r_k - c r_{k-1} + alpha w_k
+    s.a1_re = 1.0 + c.re - az.re; s.a1_im = c.im - az.im;
     s.g_re = g.re; s.g_im = g.im;
     s.nrm = nrm;
     s.k = k + 1;
