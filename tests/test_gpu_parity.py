@@ -544,3 +544,39 @@ def test_hv_sampled_rows_large_clusters(ftk, n, prec):
     ref = rows.hv_rows(cl, K, J, lambda idx: hashed_amplitudes(idx, seed), xs)
     assert n_pass >= 3
     assert rel(got, ref) <= (1e-12 if prec == "df" else 1e-6)
+
+
+def test_batched_configuration_structure(ftk):
+    """The batched configuration's structure at 12 sites: 2 seeded TPQ
+    samples x 3 spin components x all 6 momenta = 36 right-hand sides, one
+    sample as a single block of 18 and the other in blocks of 4 (and 2), FP64.
+    Every Green's function against the oracle's textbook shifted COCG of the
+    same probe (1e-8 of max |G|, tol 1e-10)."""
+    cl = named(12)
+    K, J, eta = -1.0, 0.1, 0.1
+    omega = omega_grid(-2, 2, 64)
+    ctx = ftk.Context(cl, K, J, "fp64", max_rhs=32, n_saved=2)
+    probes = [(g, qi) for g in range(3) for qi in range(len(cl.momenta))]
+    for sample, blocks in ((0, [18]), (1, [4, 4, 4, 4, 2])):
+        psi0 = random_state(12, 300 + sample)
+        ctx.set_state(psi0, 0.5)
+        ctx.tpq_step(1, 1)
+        steps, en = ctx.shells()
+        shell = len(steps) - 1
+        for slot, (g, qi) in enumerate(probes):
+            ctx.apply_op(shell, g, cl.momenta[qi], slot)
+        G = np.zeros((len(probes), omega.size), dtype=np.complex128)
+        s0 = 0
+        for width in blocks:
+            slots = list(range(s0, s0 + width))
+            Gb, itb, st = ctx.shifted_cocg(slots, omega, eta, tol=1e-10, max_iter=5000)
+            assert st == 0
+            G[s0:s0 + width] = Gb
+            s0 += width
+        z = en[shell] + omega + 1j * eta
+        for slot, (g, qi) in enumerate(probes):
+            lam = sparse.apply_op(cl, g, cl.momenta[qi], psi0)
+            Gr, itr, _, st = sparse.cocg(cl, K, J, lam, z[32], z, 1e-10, 5000)
+            assert st == 0
+            assert np.abs(G[slot] - Gr).max() <= 1e-8 * np.abs(Gr).max()
+    ctx.close()
