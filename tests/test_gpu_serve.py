@@ -99,3 +99,38 @@ def test_packed_jobs_equal_alone(prec):
         for key in a.spectra:
             assert np.linalg.norm(a.spectra[key] - m.spectra[key]) <= 1e-9 * np.linalg.norm(a.spectra[key])
             assert a.trunc[key].tolist() == m.trunc[key].tolist()
+
+
+def test_large_cluster_jobs():
+    """The serving configuration's larger clusters through the server: a
+    26-site double-float job and a 30-site job (2^30 amplitudes) in the mixed
+    mode (FP32 H.v, double-float residuals; the FP32 mode's residual stalls
+    above 1e-3 on this cluster's infinite-temperature shell), admitted by
+    footprint and run concurrently. No oracle solve fits these sizes; the
+    Green's functions must be those of a Hermitian H with eta > 0 (Im G < 0
+    at every shift; -Im G is eta |(z - H)^-1 lambda|^2) and the reweighted
+    spectra non-negative and finite."""
+    from paper_1802_02854_gb300 import build
+    build.build()
+    from paper_1802_02854_gb300 import serve
+
+    specs = [serve.JobSpec(n_sites=26, K=-1.0, J=0.1, seed=7, n_steps=21, save_every=20, probes=[(2, 1)],
+                           omega=(-3, 3, 48), eta=0.2, temps=[2.0, 4.0], tol=1e-4, max_iter=3000, block=1,
+                           precision="df"),
+             serve.JobSpec(n_sites=30, K=-1.0, J=-0.1, seed=8, n_steps=21, save_every=20, probes=[(2, 2)],
+                           omega=(-3, 3, 32), eta=0.2, temps=[2.0, 4.0], tol=1e-4, max_iter=3000, block=1,
+                           precision="mixed")]
+    srv = serve.Server(max_slots=2)
+    ids = [srv.submit(sp) for sp in specs]
+    res = [srv.result(j, timeout=1200) for j in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["peak_mem_bytes"] >= max(sp.footprint() for sp in specs)
+    for sp, r in zip(specs, res):
+        assert r.status == "ok", r.status
+        for key, G in r.G.items():
+            G = np.asarray(G)
+            assert np.isfinite(G).all()
+            assert (G.imag < 0).all(), (sp.n_sites, G.imag.max())
+            S = np.asarray(r.spectra[key])
+            assert np.isfinite(S).all() and S.min() >= -1e-9 * np.abs(S).max()
