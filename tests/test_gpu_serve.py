@@ -110,10 +110,12 @@ def test_large_cluster_jobs():
     Green's functions must be those of a Hermitian H with eta > 0 (Im G < 0
     at every shift; -Im G is eta |(z - H)^-1 lambda|^2) and the reweighted
     spectra non-negative and finite."""
+    import torch
     from paper_1802_02854_gb300 import build
     build.build()
     from paper_1802_02854_gb300 import serve
 
+    torch.cuda.empty_cache()   # the server's budget is 90 % of the memory free now
     specs = [serve.JobSpec(n_sites=26, K=-1.0, J=0.1, seed=7, n_steps=21, save_every=20, probes=[(2, 1)],
                            omega=(-3, 3, 48), eta=0.2, temps=[2.0, 4.0], tol=1e-4, max_iter=3000, block=1,
                            precision="df"),
